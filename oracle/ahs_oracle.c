@@ -1,0 +1,405 @@
+/* Adaptive Hybrid Sort (arXiv 2506.20677): CPU oracle — TEST INFRASTRUCTURE ONLY.
+ * See ahs_oracle.h for who may load this file.  Plain C99 + __int128, one
+ * thread, no blocking or fusion beyond what each cited definition states.
+ */
+#include "ahs_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 val_t;              /* the mathematical value of a key */
+typedef unsigned __int128 uval_t;
+
+/* ---------------------------------------------------------------- helpers */
+
+static int valid_type(int t) { return t >= ORC_U32 && t <= ORC_I64; }
+
+static val_t load_key(const void* keys, uint64_t i, int t) {
+    switch (t) {
+    case ORC_U32: return (val_t)((const uint32_t*)keys)[i];
+    case ORC_U64: return (val_t)((const uint64_t*)keys)[i];
+    case ORC_I32: return (val_t)((const int32_t*)keys)[i];
+    default:      return (val_t)((const int64_t*)keys)[i];
+    }
+}
+
+static void store_key(void* keys, uint64_t i, int t, val_t v) {
+    switch (t) {
+    case ORC_U32: ((uint32_t*)keys)[i] = (uint32_t)v; break;
+    case ORC_U64: ((uint64_t*)keys)[i] = (uint64_t)v; break;
+    case ORC_I32: ((int32_t*)keys)[i] = (int32_t)v; break;
+    default:      ((int64_t*)keys)[i] = (int64_t)v; break;
+    }
+}
+
+static uint64_t key_bits(val_t v, int t) {
+    switch (t) {
+    case ORC_U32: return (uint64_t)(uint32_t)v;
+    case ORC_I32: return (uint64_t)(uint32_t)(int32_t)v;
+    default:      return (uint64_t)v; /* two's complement bits of u64 / i64 */
+    }
+}
+
+static val_t* load_all(const void* keys, uint64_t n, int t) {
+    val_t* a = (val_t*)malloc((n ? n : 1) * sizeof(val_t));
+    if (!a) return NULL;
+    for (uint64_t i = 0; i < n; ++i) a[i] = load_key(keys, i, t);
+    return a;
+}
+
+static void store_all(void* keys, const val_t* a, uint64_t n, int t) {
+    for (uint64_t i = 0; i < n; ++i) store_key(keys, i, t, a[i]);
+}
+
+static uint32_t bitlen_u64(uint64_t x) {
+    uint32_t b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+/* --------------------------------------------- Section III-A: the state vector */
+
+/* n = |arr|; k = max - min + 1; H = -sum_i p_i log2 p_i (Section III-A, III-H).
+ * The sum runs over the bins j = (x - min) >> s of a histogram with at most
+ * 2^16 bins, s = max(0, bitlen(max - min) - 16): for k <= 2^16 these bins are
+ * the key values themselves and H is the paper's per-value entropy. */
+int orc_features(const void* keys, uint64_t n, int t, orc_features_t* f) {
+    if (!f || !valid_type(t) || (n && !keys)) return ORC_EINVAL;
+    memset(f, 0, sizeof(*f));
+    f->n = n;
+    if (n == 0) { f->nbins = 0; return ORC_OK; }
+
+    val_t mn = load_key(keys, 0, t), mx = mn;
+    uint64_t descents = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        val_t x = load_key(keys, i, t);
+        if (x < mn) mn = x;
+        if (x > mx) mx = x;
+        if (i + 1 < n && x > load_key(keys, i + 1, t)) ++descents;
+    }
+    uint64_t span = (uint64_t)(mx - mn);
+    uint32_t bl = bitlen_u64(span);
+    uint32_t s = bl > 16 ? bl - 16 : 0;
+    uint64_t nbins = (span >> s) + 1;
+
+    uint64_t* c = (uint64_t*)calloc(nbins, sizeof(uint64_t));
+    if (!c) return ORC_ENOMEM;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t u = (uint64_t)(load_key(keys, i, t) - mn);
+        c[u >> s] += 1;
+    }
+    double H = 0.0;
+    for (uint64_t j = 0; j < nbins; ++j) {
+        if (c[j] == 0) continue;           /* 0 log 0 = 0 */
+        double p = (double)c[j] / (double)n;
+        H -= p * log2(p);
+    }
+    free(c);
+
+    f->min_bits = key_bits(mn, t);
+    f->max_bits = key_bits(mx, t);
+    f->span = span;
+    f->shift = s;
+    f->nbins = (uint32_t)nbins;
+    f->entropy = H;
+    f->entropy_norm = nbins > 1 ? H / log2((double)nbins) : 0.0;
+    f->descents = descents;
+    return ORC_OK;
+}
+
+static int cmp_val(const void* a, const void* b) {
+    val_t x = *(const val_t*)a, y = *(const val_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* The per-value entropy over all k values (no binning): sort, then count runs. */
+int orc_entropy_exact(const void* keys, uint64_t n, int t, double* out) {
+    if (!out || !valid_type(t)) return ORC_EINVAL;
+    *out = 0.0;
+    if (n == 0) return ORC_OK;
+    val_t* a = load_all(keys, n, t);
+    if (!a) return ORC_ENOMEM;
+    qsort(a, n, sizeof(val_t), cmp_val);
+    double H = 0.0;
+    uint64_t run = 1;
+    for (uint64_t i = 1; i <= n; ++i) {
+        if (i < n && a[i] == a[i - 1]) { ++run; continue; }
+        double p = (double)run / (double)n;
+        H -= p * log2(p);
+        run = 1;
+    }
+    free(a);
+    *out = H;
+    return ORC_OK;
+}
+
+/* ------------------------------------- Section III-A, Listing 6: the decision FSM */
+
+int orc_select(const orc_features_t* f, const orc_fsm_t* p) {
+    if (f->n <= 1) return ORC_IDENTITY;                          /* Section I, III-K */
+    if (p->sorted_identity && f->descents == 0) return ORC_IDENTITY;
+    if (f->n <= p->n_t) return ORC_SMALL;                       /* n <= 20: insertion */
+    if (f->span == 0) return ORC_IDENTITY;                       /* k == 1 (III-K) */
+    uval_t k = (uval_t)f->span + 1;
+    if (k <= (uval_t)p->k_t) return ORC_COUNTING;               /* k <= 1000 */
+    if (k > (uval_t)p->k_max && (!p->use_entropy || f->entropy_norm < p->h_max))
+        return ORC_RADIX;                                        /* k > 10^6, H < 0.7 log2 k */
+    return ORC_GENERAL;                                          /* quicksort */
+}
+
+/* Eq. 4: d = ceil(log_256 k), computed by repeated division. */
+uint32_t orc_radix_passes(uint64_t span) {
+    uval_t k = (uval_t)span + 1;
+    uint32_t d = 0;
+    uval_t reach = 1;            /* 256^d */
+    while (reach < k) { reach *= 256; ++d; }
+    return d;
+}
+
+/* ---------------------------------------------------- Listing 1: insertion sort */
+
+static void insertion_core(val_t* a, uint32_t* v, uint64_t n) {
+    for (uint64_t i = 1; i < n; ++i) {
+        val_t key = a[i];
+        uint32_t kv = v ? v[i] : 0;
+        uint64_t j = i;                      /* j - 1 plays the listing's j */
+        while (j > 0 && a[j - 1] > key) {    /* strict > keeps equal keys in order */
+            a[j] = a[j - 1];
+            if (v) v[j] = v[j - 1];
+            --j;
+        }
+        a[j] = key;
+        if (v) v[j] = kv;
+    }
+}
+
+int orc_insertion_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
+                       uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    val_t* a = load_all(keys, n, t);
+    if (!a) return ORC_ENOMEM;
+    if (vals) memcpy(vals_out, vals, n * sizeof(uint32_t));
+    insertion_core(a, vals ? vals_out : NULL, n);
+    store_all(out, a, n, t);
+    free(a);
+    return ORC_OK;
+}
+
+/* ----------------------------------------------------- Listing 2: counting sort */
+
+/* Count[i] = #{j : A[j] - min = i}; prefix sums; then a reverse scan that places
+ * A[j] at Count[A[j] - min] - 1 and decrements (stable). */
+int orc_counting_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
+                      uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    if (n == 0) return ORC_OK;
+    val_t* a = load_all(keys, n, t);
+    if (!a) return ORC_ENOMEM;
+    val_t mn = a[0], mx = a[0];
+    for (uint64_t i = 0; i < n; ++i) { if (a[i] < mn) mn = a[i]; if (a[i] > mx) mx = a[i]; }
+    uval_t range = (uval_t)(mx - mn) + 1;
+    if (range > ((uval_t)1 << 28)) { free(a); return ORC_ERANGE; }
+    uint64_t* count = (uint64_t*)calloc((size_t)range, sizeof(uint64_t));
+    val_t* o = (val_t*)malloc(n * sizeof(val_t));
+    if (!count || !o) { free(a); free(count); free(o); return ORC_ENOMEM; }
+    for (uint64_t i = 0; i < n; ++i) count[(uint64_t)(a[i] - mn)] += 1;
+    for (uint64_t i = 1; i < (uint64_t)range; ++i) count[i] += count[i - 1];
+    for (uint64_t i = n; i-- > 0;) {
+        uint64_t c = (uint64_t)(a[i] - mn);
+        uint64_t pos = count[c] - 1;
+        o[pos] = a[i];
+        if (vals) vals_out[pos] = vals[i];
+        count[c] -= 1;
+    }
+    store_all(out, o, n, t);
+    free(a); free(count); free(o);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------- Listing 3: LSD radix sort */
+
+/* LSD over u = x - min in base 256 (the base the paper uses for k > 10^6),
+ * d = ceil(log_256 k) passes (Eq. 4).  Each pass distributes the keys into 256
+ * buckets in input order and concatenates the buckets (stable). */
+static int radix_core(val_t* a, uint32_t* v, uint64_t n) {
+    if (n == 0) return ORC_OK;
+    val_t mn = a[0], mx = a[0];
+    for (uint64_t i = 0; i < n; ++i) { if (a[i] < mn) mn = a[i]; if (a[i] > mx) mx = a[i]; }
+    uint32_t d = orc_radix_passes((uint64_t)(mx - mn));
+    val_t* ta = (val_t*)malloc(n * sizeof(val_t));
+    uint32_t* tv = v ? (uint32_t*)malloc(n * sizeof(uint32_t)) : NULL;
+    if (!ta || (v && !tv)) { free(ta); free(tv); return ORC_ENOMEM; }
+    for (uint32_t digit = 0; digit < d; ++digit) {
+        uint64_t bucket_size[256] = {0}, bucket_start[256];
+        for (uint64_t i = 0; i < n; ++i) {
+            uint64_t u = (uint64_t)(a[i] - mn);
+            bucket_size[(u >> (8 * digit)) & 255] += 1;
+        }
+        uint64_t acc = 0;
+        for (int b = 0; b < 256; ++b) { bucket_start[b] = acc; acc += bucket_size[b]; }
+        for (uint64_t i = 0; i < n; ++i) {           /* append in input order */
+            uint64_t u = (uint64_t)(a[i] - mn);
+            uint64_t pos = bucket_start[(u >> (8 * digit)) & 255]++;
+            ta[pos] = a[i];
+            if (v) tv[pos] = v[i];
+        }
+        memcpy(a, ta, n * sizeof(val_t));            /* the flattened buckets */
+        if (v) memcpy(v, tv, n * sizeof(uint32_t));
+    }
+    free(ta); free(tv);
+    return ORC_OK;
+}
+
+int orc_radix_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
+                   uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    val_t* a = load_all(keys, n, t);
+    if (!a) return ORC_ENOMEM;
+    if (vals) memcpy(vals_out, vals, n * sizeof(uint32_t));
+    int rc = radix_core(a, vals ? vals_out : NULL, n);
+    if (rc == ORC_OK) store_all(out, a, n, t);
+    free(a);
+    return rc;
+}
+
+/* Listing 7 (keys only): split negatives and non-negatives, sort the absolute
+ * values of the negatives and the non-negatives separately, reverse the
+ * former, restore their sign and concatenate.  Negation is exact in 128 bits. */
+int orc_radix_sort_signed_listing7(const void* keys, void* out, uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    val_t* a = load_all(keys, n, t);
+    val_t* neg = (val_t*)malloc((n ? n : 1) * sizeof(val_t));
+    val_t* pos = (val_t*)malloc((n ? n : 1) * sizeof(val_t));
+    if (!a || !neg || !pos) { free(a); free(neg); free(pos); return ORC_ENOMEM; }
+    uint64_t nn = 0, np = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (a[i] < 0) neg[nn++] = -a[i];
+        else pos[np++] = a[i];
+    }
+    int rc = radix_core(neg, NULL, nn);
+    if (rc == ORC_OK) rc = radix_core(pos, NULL, np);
+    if (rc == ORC_OK) {
+        uint64_t o = 0;
+        for (uint64_t i = nn; i-- > 0;) a[o++] = -neg[i];
+        for (uint64_t i = 0; i < np; ++i) a[o++] = pos[i];
+        store_all(out, a, n, t);
+    }
+    free(a); free(neg); free(pos);
+    return rc;
+}
+
+/* ------------------------------------ Listing 4: quicksort, median-of-three pivot */
+
+static val_t median_of_three(const val_t* a, uint64_t n) {
+    val_t x = a[0], y = a[n / 2], z = a[n - 1];
+    /* the middle value of the three */
+    if (x > y) { val_t tmp = x; x = y; y = tmp; }
+    if (y > z) { val_t tmp = y; y = z; z = tmp; }
+    if (x > y) { val_t tmp = x; x = y; y = tmp; }
+    return y;
+}
+
+/* Partition into (< pivot), (== pivot), (> pivot), each in input order, as the
+ * listing's filters do; the (== pivot) group keeps every copy of the pivot. */
+static void quick_core(val_t* a, val_t* tmp, uint64_t n) {
+    while (n > 1) {
+        val_t pivot = median_of_three(a, n);
+        uint64_t nl = 0, ne = 0, ng = 0;
+        for (uint64_t i = 0; i < n; ++i) {
+            if (a[i] < pivot) ++nl;
+            else if (a[i] == pivot) ++ne;
+        }
+        ng = n - nl - ne;
+        uint64_t il = 0, ie = nl, ig = nl + ne;
+        for (uint64_t i = 0; i < n; ++i) {
+            if (a[i] < pivot) tmp[il++] = a[i];
+            else if (a[i] == pivot) tmp[ie++] = a[i];
+            else tmp[ig++] = a[i];
+        }
+        memcpy(a, tmp, n * sizeof(val_t));
+        /* recurse into the smaller side, iterate on the larger (bounded stack) */
+        if (nl < ng) {
+            quick_core(a, tmp, nl);
+            a += nl + ne; tmp += nl + ne; n = ng;
+        } else {
+            quick_core(a + nl + ne, tmp + nl + ne, ng);
+            n = nl;
+        }
+    }
+}
+
+int orc_quicksort(const void* keys, void* out, uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    val_t* a = load_all(keys, n, t);
+    val_t* tmp = (val_t*)malloc((n ? n : 1) * sizeof(val_t));
+    if (!a || !tmp) { free(a); free(tmp); return ORC_ENOMEM; }
+    quick_core(a, tmp, n);
+    store_all(out, a, n, t);
+    free(a); free(tmp);
+    return ORC_OK;
+}
+
+/* ------------------------------------- stable merge sort (general path, payload) */
+
+static void merge_core(val_t* a, uint32_t* v, val_t* ta, uint32_t* tv, uint64_t n) {
+    if (n < 2) return;
+    uint64_t h = n / 2;
+    merge_core(a, v, ta, tv, h);
+    merge_core(a + h, v ? v + h : NULL, ta, tv, n - h);
+    uint64_t i = 0, j = h, o = 0;
+    while (i < h && j < n) {
+        if (a[j] < a[i]) { ta[o] = a[j]; if (v) tv[o] = v[j]; ++j; }   /* ties take the left */
+        else             { ta[o] = a[i]; if (v) tv[o] = v[i]; ++i; }
+        ++o;
+    }
+    while (i < h) { ta[o] = a[i]; if (v) tv[o] = v[i]; ++i; ++o; }
+    while (j < n) { ta[o] = a[j]; if (v) tv[o] = v[j]; ++j; ++o; }
+    memcpy(a, ta, n * sizeof(val_t));
+    if (v) memcpy(v, tv, n * sizeof(uint32_t));
+}
+
+int orc_merge_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
+                   uint64_t n, int t) {
+    if (!valid_type(t)) return ORC_EINVAL;
+    val_t* a = load_all(keys, n, t);
+    val_t* ta = (val_t*)malloc((n ? n : 1) * sizeof(val_t));
+    uint32_t* tv = vals ? (uint32_t*)malloc((n ? n : 1) * sizeof(uint32_t)) : NULL;
+    if (!a || !ta || (vals && !tv)) { free(a); free(ta); free(tv); return ORC_ENOMEM; }
+    if (vals) memcpy(vals_out, vals, n * sizeof(uint32_t));
+    merge_core(a, vals ? vals_out : NULL, ta, tv, n);
+    store_all(out, a, n, t);
+    free(a); free(ta); free(tv);
+    return ORC_OK;
+}
+
+/* -------------------------------------------------------- the whole pipeline */
+
+int orc_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
+             uint64_t n, int t, int force, const orc_fsm_t* fsm,
+             int* chosen, orc_features_t* feat) {
+    if (!valid_type(t) || force < ORC_AUTO || force > ORC_GENERAL) return ORC_EINVAL;
+    orc_features_t f;
+    int rc = orc_features(keys, n, t, &f);
+    if (rc != ORC_OK) return rc;
+    if (feat) *feat = f;
+    int s = force;
+    if (s == ORC_AUTO) {
+        if (!fsm) return ORC_EINVAL;
+        s = orc_select(&f, fsm);
+    }
+    if (chosen) *chosen = s;
+    size_t w = (t == ORC_U32 || t == ORC_I32) ? 4 : 8;
+    switch (s) {
+    case ORC_IDENTITY:
+        if (n) memmove(out, keys, n * w);
+        if (vals && n) memmove(vals_out, vals, n * sizeof(uint32_t));
+        return ORC_OK;
+    case ORC_SMALL:    return orc_insertion_sort(keys, out, vals, vals_out, n, t);
+    case ORC_COUNTING: return orc_counting_sort(keys, out, vals, vals_out, n, t);
+    case ORC_RADIX:    return orc_radix_sort(keys, out, vals, vals_out, n, t);
+    default:
+        if (vals) return orc_merge_sort(keys, out, vals, vals_out, n, t);
+        return orc_quicksort(keys, out, n, t);
+    }
+}
