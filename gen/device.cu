@@ -1,0 +1,141 @@
+// Seeded synthetic workloads, device side: the same counter-based definitions
+// as gen/host.py, bit for bit (SplitMix64 output function on a counter,
+// Lemire multiply-shift for bounded integers).  Inputs only: nothing here is
+// part of the sorting method.  Built as gen/libahsgen.so, separate from the
+// sorting library.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr unsigned long long kGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ unsigned long long stream_key(unsigned long long seed,
+                                                                  unsigned long long stream) {
+    return mix64(seed * kGolden + mix64(stream + kGolden));
+}
+
+__device__ __forceinline__ unsigned long long draw(unsigned long long key, unsigned long long i) {
+    return mix64(key + (i + 1) * kGolden);
+}
+
+__global__ void k_uniform_u32(uint32_t* out, unsigned long long n, unsigned long long key,
+                              unsigned long long m, unsigned long long start) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride)
+        out[i] = (uint32_t)(((draw(key, start + i) >> 32) * m) >> 32);
+}
+
+__global__ void k_zipf_u32(uint32_t* out, unsigned long long n, unsigned long long key,
+                           const double* cdf, const uint32_t* values, uint32_t nv,
+                           unsigned long long start) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        const double u = (double)(draw(key, start + i) >> 11) * 0x1.0p-53;
+        // first index with cdf[idx] > u
+        uint32_t lo = 0, hi = nv;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cdf[mid] > u) hi = mid;
+            else lo = mid + 1;
+        }
+        out[i] = values[lo < nv ? lo : nv - 1];
+    }
+}
+
+__global__ void k_ramp_steps(unsigned long long* out, unsigned long long n, unsigned long long key,
+                             unsigned long long m) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride)
+        out[i] = i == 0 ? 0ull : __umul64hi(draw(key, i), m);
+}
+
+__global__ void k_ramp_replace(unsigned long long* t, unsigned long long n, unsigned long long key_p,
+                               unsigned long long key_v, unsigned long long thresh53,
+                               unsigned long long t0, unsigned long long range) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        if ((draw(key_p, i) >> 11) < thresh53) {
+            const unsigned long long r = draw(key_v, i);
+            t[i] = t0 + (range == 0 ? r : __umul64hi(r, range));
+        }
+    }
+}
+
+// Sequential swaps of (i, j) pairs: one thread keeps the sequential semantics.
+__global__ void k_swaps_u32(uint32_t* a, unsigned long long n, unsigned long long swaps,
+                            unsigned long long key) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (unsigned long long t = 0; t < swaps; ++t) {
+        const unsigned long long i = __umul64hi(draw(key, 2 * t), n);
+        const unsigned long long j = __umul64hi(draw(key, 2 * t + 1), n);
+        const uint32_t x = a[i];
+        a[i] = a[j];
+        a[j] = x;
+    }
+}
+
+unsigned grid(unsigned long long n) {
+    unsigned long long g = (n + 255) / 256;
+    return (unsigned)(g < 8192 ? (g ? g : 1) : 8192);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gen_uniform_u32(void* out, unsigned long long n, unsigned long long seed,
+                    unsigned long long stream, unsigned long long m, unsigned long long start,
+                    void* st) {
+    if (n == 0) return 0;
+    k_uniform_u32<<<grid(n), 256, 0, (cudaStream_t)st>>>((uint32_t*)out, n, stream_key(seed, stream),
+                                                         m, start);
+    return (int)cudaGetLastError();
+}
+
+int gen_zipf_u32(void* out, unsigned long long n, unsigned long long seed, unsigned long long stream,
+                 const void* d_cdf, const void* d_values, unsigned nv, unsigned long long start,
+                 void* st) {
+    if (n == 0) return 0;
+    k_zipf_u32<<<grid(n), 256, 0, (cudaStream_t)st>>>((uint32_t*)out, n, stream_key(seed, stream),
+                                                      (const double*)d_cdf, (const uint32_t*)d_values,
+                                                      nv, start);
+    return (int)cudaGetLastError();
+}
+
+int gen_ramp_steps(void* out, unsigned long long n, unsigned long long seed, unsigned long long m,
+                   void* st) {
+    if (n == 0) return 0;
+    k_ramp_steps<<<grid(n), 256, 0, (cudaStream_t)st>>>((unsigned long long*)out, n,
+                                                        stream_key(seed, 1), m);
+    return (int)cudaGetLastError();
+}
+
+int gen_ramp_replace(void* t, unsigned long long n, unsigned long long seed,
+                     unsigned long long thresh53, unsigned long long t0, unsigned long long range,
+                     void* st) {
+    if (n == 0) return 0;
+    k_ramp_replace<<<grid(n), 256, 0, (cudaStream_t)st>>>((unsigned long long*)t, n,
+                                                          stream_key(seed, 2), stream_key(seed, 3),
+                                                          thresh53, t0, range);
+    return (int)cudaGetLastError();
+}
+
+int gen_swaps_u32(void* a, unsigned long long n, unsigned long long swaps, unsigned long long seed,
+                  unsigned long long stream, void* st) {
+    if (n == 0 || swaps == 0) return 0;
+    k_swaps_u32<<<1, 1, 0, (cudaStream_t)st>>>((uint32_t*)a, n, swaps, stream_key(seed, stream));
+    return (int)cudaGetLastError();
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+"""Seeded synthetic workloads generated on the GPU (bit-identical to gen/host.py).
+
+Returns CUDA tensors with int32 / int64 dtype holding the uint32 / uint64 bits.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from gen import host as H
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "libahsgen.so")
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise ImportError(f"{_LIB} missing: run gen/build.py")
+        L = ctypes.CDLL(_LIB)
+        u64, vp = ctypes.c_uint64, ctypes.c_void_p
+        L.gen_uniform_u32.argtypes = [vp, u64, u64, u64, u64, u64, vp]
+        L.gen_zipf_u32.argtypes = [vp, u64, u64, u64, vp, vp, ctypes.c_uint, u64, vp]
+        L.gen_ramp_steps.argtypes = [vp, u64, u64, u64, vp]
+        L.gen_ramp_replace.argtypes = [vp, u64, u64, u64, u64, u64, vp]
+        L.gen_swaps_u32.argtypes = [vp, u64, u64, u64, u64, vp]
+        _lib = L
+    return _lib
+
+
+def _st():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ok(rc):
+    if rc != 0:
+        raise RuntimeError(f"generator launch failed ({rc})")
+
+
+def uniform_u32(n, seed, stream, m, start=0):
+    import torch
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    _ok(lib().gen_uniform_u32(out.data_ptr(), n, seed, stream, m, start, _st()))
+    return out
+
+
+def zipf_u32(n, seed, stream_values, stream_ranks, n_values=1024, s=1.1, start=0):
+    import torch
+    cdf = torch.from_numpy(H.zipf_cdf(n_values, s)).cuda()
+    vals = torch.from_numpy(H.zipf_values(seed, stream_values, n_values).view(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    _ok(lib().gen_zipf_u32(out.data_ptr(), n, seed, stream_ranks, cdf.data_ptr(), vals.data_ptr(),
+                           n_values, start, _st()))
+    torch.cuda.synchronize()
+    return out
+
+
+def sorted_u32(x):
+    """Ascending order of uint32 bits held in an int32 tensor."""
+    import torch
+    s = torch.sort(x.to(torch.int64) & 0xFFFFFFFF).values
+    return s.to(torch.int32)
+
+
+def swaps_u32(a, n_swaps, seed, stream):
+    _ok(lib().gen_swaps_u32(a.data_ptr(), a.numel(), n_swaps, seed, stream, _st()))
+    return a
+
+
+def config1(n=H.N_CFG1):
+    return uniform_u32(n, H.SEED_CFG1, 0, 256)
+
+
+def config2(variant, n=H.N_CFG2, seed=H.SEED_CFG2):
+    import torch
+    if variant == "a":
+        return uniform_u32(n, seed, 1, 4096)
+    if variant == "b":
+        return zipf_u32(n, seed, 2, 3)
+    if variant == "c":
+        return uniform_u32(n, seed, 4, 1 << 32)
+    base = sorted_u32(uniform_u32(n, seed, 4, 1 << 32))
+    if variant == "d":
+        return base
+    if variant == "e":
+        return swaps_u32(base, n // 100, seed, 5)
+    if variant == "f":
+        return torch.flip(base, dims=[0]).contiguous()
+    raise ValueError(variant)
+
+
+def config3(n=H.N_CFG3, seed=H.SEED_CFG3, t0=1_700_000_000_000_000_000, max_step=1000):
+    """uint64 ramp keys (int64 tensor) and uint32 payload = index (int32 tensor)."""
+    import torch
+    steps = torch.empty(n, dtype=torch.int64, device="cuda")
+    _ok(lib().gen_ramp_steps(steps.data_ptr(), n, seed, max_step + 1, _st()))
+    t = torch.cumsum(steps, 0) + t0
+    last = int(t[-1].item())
+    rng = last - t0 + 1
+    _ok(lib().gen_ramp_replace(t.data_ptr(), n, seed, H.REPLACE_53, t0, rng % (1 << 64), _st()))
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    return t, vals

@@ -1,0 +1,268 @@
+/* ahs.h — C ABI of the GB300 (sm_103a) Adaptive Hybrid Sort library.
+ *
+ * Adaptive Hybrid Sort (arXiv 2506.20677) sorts an array of integer keys by
+ * first extracting the state vector v = (n, k, H) (Section III-A: size, value
+ * range k = max - min + 1, Shannon entropy H of the key histogram), then
+ * choosing a strategy with a finite-state machine (Section III-A, Listing 6)
+ * or a trained tree classifier (Section III-H), then running insertion,
+ * counting (Listing 2), LSD radix (Listing 3) or a general comparison-class
+ * sort (Listing 4: quicksort; here a splitter-based sample sort).
+ *
+ * Conventions for every function below:
+ *  - All functions are extern "C", never throw, and return ahs_status.
+ *  - "d_" pointers are CUDA device pointers on the context's device; "h_"
+ *    pointers are host pointers.  The caller owns every key / payload buffer.
+ *  - Keys are exact integers: AHS_U32, AHS_I32 (4 bytes) or AHS_U64, AHS_I64
+ *    (8 bytes), contiguous, any alignment of the element type.  Signed keys
+ *    sort in signed order.  An optional payload is uint32 per key.
+ *  - Non-integer inputs are refused (Section III-K): bindings map float
+ *    dtypes to AHS_ERR_DTYPE; an unknown ahs_key_type is AHS_ERR_DTYPE.
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on that stream; functions that return host
+ *    results synchronise that stream and say so.
+ *  - A context is single-threaded: calls on one ctx must not overlap, except
+ *    ahs_serve_submit / ahs_serve_poll, which are thread-safe.
+ *  - Device-side waits (decoupled look-back) are bounded; a wait that runs out
+ *    returns AHS_ERR_DEVICE_TIMEOUT and leaves the context usable.
+ */
+#ifndef AHS_H
+#define AHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AHS_VERSION_MAJOR 0
+#define AHS_VERSION_MINOR 1
+
+typedef enum {
+    AHS_OK = 0,
+    AHS_ERR_INVALID_ARG = 1,    /* bad pointer, size, enum value or combination */
+    AHS_ERR_DTYPE = 2,          /* keys are not one of the four integer types (Section III-K) */
+    AHS_ERR_OOM = 3,            /* device workspace could not be allocated */
+    AHS_ERR_BUDGET = 4,         /* a served request can never fit the HBM budget */
+    AHS_ERR_CUDA = 5,           /* a CUDA runtime call failed (see ahs_last_cuda_error) */
+    AHS_ERR_DEVICE_TIMEOUT = 6, /* a bounded device-side wait ran out */
+    AHS_ERR_AGAIN = 7,          /* a served request is not finished yet */
+    AHS_ERR_NOT_FOUND = 8,      /* unknown ticket / file */
+    AHS_ERR_UNIMPLEMENTED = 9,  /* strategy / type combination not provided */
+    AHS_ERR_RANGE = 10          /* forced strategy cannot handle this input's range or size */
+} ahs_status;
+
+typedef enum { AHS_U32 = 0, AHS_U64 = 1, AHS_I32 = 2, AHS_I64 = 3 } ahs_key_type;
+
+/* Strategies of Section III-D..G.  IDENTITY copies (n < 2, k == 1, or an input
+ * already in order under a profile that checks it). */
+typedef enum {
+    AHS_AUTO = 0, AHS_IDENTITY = 1, AHS_SMALL = 2, AHS_COUNTING = 3,
+    AHS_RADIX = 4, AHS_GENERAL = 5
+} ahs_strategy;
+
+/* Selector profiles.
+ *  PAPER:    the FSM of Section III-A with n_t = 20, k_t = 1000, k_max = 10^6 and
+ *            the entropy test H < 0.7 log2 k, evaluated as h = H / log2(nbins) < 0.7.
+ *  LISTING6: the same thresholds without the entropy test (Listing 6).
+ *  GB300:    the same chain with k_t = 65,536 (the largest range whose counting
+ *            histogram is the feature histogram itself, the analogue of Eq. 2),
+ *            n_t = the one-block sort capacity, and "already in order" -> IDENTITY.
+ *  MODEL:    n < 1000 -> GB300 rules; otherwise a tree ensemble evaluated on
+ *            (log2 n, log2 k, h, key bytes, has payload) (Section III-H, Table IV).
+ *  CUSTOM:   the thresholds given in ahs_config_t.thresholds. */
+typedef enum {
+    AHS_SEL_PAPER = 0, AHS_SEL_LISTING6 = 1, AHS_SEL_GB300 = 2, AHS_SEL_MODEL = 3,
+    AHS_SEL_CUSTOM = 4
+} ahs_select_mode;
+
+/* The state vector of Section III-A with the histogram binning it was taken on.
+ * min_bits / max_bits are the smallest / largest key's own bit pattern,
+ * zero-extended to 64 bits.  span = max - min as an integer (k = span + 1).
+ * The histogram has nbins = (span >> hist_shift) + 1 <= 65,536 bins of
+ * (key - min) >> hist_shift, hist_shift = max(0, bitlen(span) - 16); for
+ * k <= 65,536 the bins are the key values.  entropy_bits = -sum p log2 p over
+ * non-empty bins (fp64), entropy_norm = entropy_bits / log2(nbins) (0 if
+ * nbins == 1).  descents = #{i : key[i] > key[i+1]} (0: already in order). */
+typedef struct {
+    uint64_t n;
+    uint64_t min_bits;
+    uint64_t max_bits;
+    uint64_t span;
+    uint32_t hist_shift;
+    uint32_t nbins;
+    double entropy_bits;
+    double entropy_norm;
+    uint64_t descents;
+} ahs_features_t;
+
+/* FSM thresholds (Section III-A, Table II).  Comparisons follow the text:
+ * n <= n_t, k <= k_t, k > k_max, h < h_max. */
+typedef struct {
+    uint64_t n_t;
+    uint64_t k_t;
+    uint64_t k_max;
+    double h_max;
+    int32_t use_entropy;
+    int32_t sorted_identity;
+} ahs_thresholds_t;
+
+typedef struct {
+    int32_t device;              /* CUDA device ordinal */
+    ahs_select_mode select_mode; /* used by ahs_sort / ahs_sort_batch with AHS_AUTO */
+    ahs_thresholds_t thresholds; /* for AHS_SEL_CUSTOM */
+    const char* model_path;      /* tree table for AHS_SEL_MODEL (NULL: none loaded) */
+    uint64_t workspace_limit;    /* bytes of device workspace the ctx may hold, 0 = no limit */
+    int32_t timing;              /* 1: record per-phase device times into info structs */
+} ahs_config_t;
+
+/* Filled by ahs_sort when non-NULL. */
+typedef struct {
+    ahs_strategy strategy;       /* the strategy that ran */
+    int32_t features_valid;      /* 1 if features below were computed */
+    ahs_features_t features;
+    uint32_t passes;             /* radix digit passes run / sample-sort partition levels */
+    uint32_t buckets;            /* final buckets sorted in shared memory (general path) */
+    float ms_features;           /* device ms of the feature pass (timing = 1) */
+    float ms_sort;               /* device ms of the strategy (timing = 1) */
+    uint64_t workspace_bytes;    /* device workspace held by the ctx after the call */
+} ahs_sort_info_t;
+
+typedef struct {
+    uint64_t n_keys;             /* total keys over all segments */
+    uint32_t n_seg;
+    uint32_t seg_per_strategy[6];/* segments per ahs_strategy value */
+    uint64_t keys_per_strategy[6];
+    float ms_features;
+    float ms_select;             /* host time of the per-segment selection */
+    float ms_sort;
+} ahs_batch_info_t;
+
+typedef struct ahs_ctx ahs_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Fill *cfg with defaults: device 0, GB300 profile, no model, no limit, no timing. */
+void ahs_default_config(ahs_config_t* cfg);
+/* Thresholds of a built-in profile (PAPER, LISTING6, GB300). */
+ahs_status ahs_profile_thresholds(ahs_select_mode mode, ahs_thresholds_t* out);
+/* Create a context on cfg->device (cfg may be NULL for defaults).  The ctx owns
+ * its device workspace, which grows on demand and is freed by ahs_destroy. */
+ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg);
+void ahs_destroy(ahs_ctx* ctx);
+const char* ahs_status_str(ahs_status s);
+/* Text of the last CUDA error seen by this ctx ("" if none). */
+const char* ahs_last_cuda_error(const ahs_ctx* ctx);
+/* Load (or replace) the MODEL profile's tree table from a text file. */
+ahs_status ahs_load_model(ahs_ctx* ctx, const char* path);
+
+/* ---------------------------------------------------------------- tracing */
+
+/* One traced kernel launch: the kernel's name (static string), the keys it
+ * processed (0 where not meaningful) and its device time from CUDA events
+ * recorded around it on the launching stream. */
+typedef struct {
+    const char* kernel;
+    uint64_t items;
+    float ms;
+} ahs_trace_entry_t;
+
+/* Turn per-launch tracing of this ctx's calls on (1) or off (0). */
+ahs_status ahs_trace_enable(ahs_ctx* ctx, int32_t on);
+/* Wait for and return the launches traced since the last collect (at most
+ * cap entries are written; *count receives how many there were), then clear. */
+ahs_status ahs_trace_collect(ahs_ctx* ctx, ahs_trace_entry_t* out, uint32_t cap, uint32_t* count);
+
+/* ------------------------------------------------ Section III-A: features */
+
+/* Compute the state vector of d_keys[0..n) on the device (three kernels: a
+ * min/max/descent reduction, the <= 2^16-bin histogram, the fp64 entropy
+ * reduction) and copy it to *h_out.  Synchronises `stream`. */
+ahs_status ahs_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_type type,
+                        void* stream, ahs_features_t* h_out);
+
+/* ------------------------------------------- Section III-A / III-H: select */
+
+/* Pure host function: the FSM with explicit thresholds. */
+ahs_status ahs_select_fsm(const ahs_features_t* f, const ahs_thresholds_t* t,
+                          ahs_strategy* out);
+/* Select with a profile (MODEL uses the ctx's loaded tree table; key_bytes and
+ * has_payload are model inputs and are ignored by the FSM profiles). */
+ahs_status ahs_select(const ahs_ctx* ctx, const ahs_features_t* f, ahs_select_mode mode,
+                      uint32_t key_bytes, int32_t has_payload, ahs_strategy* out);
+
+/* ------------------------------------------------------------ the sorts */
+
+/* Sort n keys (and their uint32 payload, stably) from d_keys_in into d_keys_out.
+ * d_keys_out may equal d_keys_in (in place); likewise d_vals_out / d_vals_in.
+ * d_vals_in == NULL means keys only (d_vals_out is then ignored).
+ * force == AHS_AUTO: features -> select (ctx's select_mode) -> strategy; the
+ * feature readback synchronises `stream` once.  A forced strategy skips the
+ * selector; AHS_COUNTING requires k <= 65,536 (AHS_ERR_RANGE otherwise) and
+ * AHS_SMALL requires n <= ahs_small_capacity(type, payload).
+ * Output: keys in non-decreasing order; payload in the unique stable order.
+ * info may be NULL. */
+ahs_status ahs_sort(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
+                    const uint32_t* d_vals_in, uint32_t* d_vals_out,
+                    uint64_t n, ahs_key_type type, ahs_strategy force,
+                    void* stream, ahs_sort_info_t* info);
+
+/* Largest n the one-block shared-memory sort (AHS_SMALL) takes. */
+uint64_t ahs_small_capacity(ahs_key_type type, int32_t has_payload);
+
+/* Sort n_seg independent segments [off[i], off[i+1]) of one key buffer, each
+ * with its own features and strategy, using one launch per strategy class.
+ * h_seg_offsets: host array of n_seg + 1 non-decreasing offsets (off[0] may be
+ * > 0; keys outside [off[0], off[n_seg]) are not touched).  Out-of-place only
+ * (d_keys_out != d_keys_in).  Payload as in ahs_sort.  Synchronises `stream`. */
+ahs_status ahs_sort_batch(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
+                          const uint32_t* d_vals_in, uint32_t* d_vals_out,
+                          const uint64_t* h_seg_offsets, uint32_t n_seg,
+                          ahs_key_type type, void* stream, ahs_batch_info_t* info);
+
+/* -------------------------------------------------------------- serving */
+
+typedef struct {
+    uint64_t budget_bytes;       /* HBM the in-flight requests may reserve */
+    uint32_t max_inflight;       /* requests on the GPU at once */
+    uint32_t tick_us;            /* scheduler period when idle */
+} ahs_serve_config_t;
+
+typedef struct {
+    const void* d_keys_in;       /* device keys, valid until the request completes */
+    void* d_keys_out;            /* device output (may equal d_keys_in) */
+    uint64_t n;
+    ahs_key_type type;
+} ahs_request_t;
+
+typedef struct {
+    ahs_status status;           /* AHS_OK once done */
+    ahs_strategy strategy;
+    double latency_ms;           /* submit -> completion observed on the host */
+    double queue_ms;             /* submit -> admission */
+} ahs_result_t;
+
+typedef struct {
+    uint64_t completed;
+    uint64_t keys;
+    double p50_ms, p99_ms;       /* latency percentiles over completed requests */
+    uint64_t peak_reserved_bytes;
+    uint64_t batches;            /* batched launches issued */
+} ahs_serve_stats_t;
+
+/* Start the scheduler thread of a serving loop on this ctx (one per ctx). */
+ahs_status ahs_serve_start(ahs_ctx* ctx, const ahs_serve_config_t* cfg);
+/* Enqueue a request; *ticket identifies it.  AHS_ERR_BUDGET if its workspace
+ * can never fit budget_bytes.  Thread-safe. */
+ahs_status ahs_serve_submit(ahs_ctx* ctx, const ahs_request_t* req, uint64_t* ticket);
+/* Wait up to timeout_ms (0: just look) for a ticket.  AHS_ERR_AGAIN if not
+ * done; on completion fills *out once and forgets the ticket.  Thread-safe. */
+ahs_status ahs_serve_poll(ahs_ctx* ctx, uint64_t ticket, int32_t timeout_ms, ahs_result_t* out);
+ahs_status ahs_serve_stats(ahs_ctx* ctx, ahs_serve_stats_t* out);
+/* Drain in-flight requests and stop the scheduler. */
+ahs_status ahs_serve_stop(ahs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AHS_H */

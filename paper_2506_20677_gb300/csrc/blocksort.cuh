@@ -1,0 +1,142 @@
+// One-CTA stable sort of up to THREADS*IPT keys (optional uint32 payload) in
+// registers and shared memory: LSD passes of 8-bit digits over u = ord(x) -
+// min, with min and the digit count taken from the keys themselves (so a
+// segment whose keys are all equal costs no pass).  Used for small inputs
+// (the paper's insertion-sort regime, Section III-E) and for the buckets of the
+// general path.
+#pragma once
+
+#include "common.cuh"
+
+namespace ahs {
+
+constexpr int kBsRadix = 256;
+
+template <typename K, bool VALS, int THREADS, int IPT>
+struct BlockSortSmem {
+    static constexpr int W = THREADS / 32;
+    static constexpr int CAP = THREADS * IPT;
+    uint32_t warp_hist[W][kBsRadix];
+    uint32_t tile_count[kBsRadix];
+    uint32_t tile_start[kBsRadix];
+    uint32_t scan[W + 1];
+    unsigned long long red[2][W];
+    K keys[CAP];
+    uint32_t vals[VALS ? CAP : 1];
+};
+
+// Sort keys_in[0..m) (m <= CAP) into keys_out[0..m); vals likewise.  All
+// threads of the block must call it.  keys_in may equal keys_out.
+template <typename K, bool VALS, int THREADS, int IPT>
+__device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
+                                           const uint32_t* vals_in, uint32_t* vals_out,
+                                           uint32_t m, K flip,
+                                           BlockSortSmem<K, VALS, THREADS, IPT>& S) {
+    constexpr int W = THREADS / 32;
+    constexpr int WARP_ITEMS = 32 * IPT;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t wbase = warp * WARP_ITEMS;
+
+    K key[IPT];
+    uint32_t val[IPT];
+    K lo = ~K(0), hi = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) {
+            key[i] = keys_in[p];
+            if constexpr (VALS) val[i] = vals_in[p];
+            const K o = key[i] ^ flip;
+            lo = o < lo ? o : lo;
+            hi = o > hi ? o : hi;
+        } else {
+            key[i] = 0;
+            if constexpr (VALS) val[i] = 0;
+        }
+    }
+    // Block min / max of ord(x).
+    {
+        unsigned long long a = warp_min((unsigned long long)lo), b = warp_max((unsigned long long)hi);
+        if (lane == 0) { S.red[0][warp] = a; S.red[1][warp] = b; }
+        __syncthreads();
+        a = S.red[0][0];
+        b = S.red[1][0];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            a = S.red[0][w] < a ? S.red[0][w] : a;
+            b = S.red[1][w] > b ? S.red[1][w] : b;
+        }
+        lo = (K)a;
+        hi = (K)b;
+        __syncthreads();
+    }
+    const uint32_t D = m ? bitlen64((unsigned long long)(K)(hi - lo)) : 0;
+    const uint32_t passes = (D + 7) / 8;
+    const uint32_t lt = lanemask_lt();
+
+    for (uint32_t pass = 0; pass < passes; ++pass) {
+        const uint32_t shift = 8 * pass;
+        for (uint32_t i = tid; i < W * kBsRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t dig[IPT], rank[IPT];
+        uint32_t* wh = S.warp_hist[warp];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint32_t p = wbase + 32 * i + lane;
+            dig[i] = p < m ? (uint32_t)(((K)(key[i] ^ flip) - lo) >> shift) & 0xffu : (uint32_t)kBsRadix;
+            const uint32_t peers = __match_any_sync(AHS_FULL_MASK, dig[i]);
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader && dig[i] < (uint32_t)kBsRadix) old = atomicAdd(&wh[dig[i]], __popc(peers));
+            old = __shfl_sync(AHS_FULL_MASK, old, leader);
+            rank[i] = old + __popc(peers & lt);
+        }
+        __syncthreads();
+        for (uint32_t d = tid; d < (uint32_t)kBsRadix; d += THREADS) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint32_t c = S.warp_hist[w][d];
+                S.warp_hist[w][d] = run;
+                run += c;
+            }
+            S.tile_count[d] = run;
+        }
+        __syncthreads();
+        {
+            uint32_t total;
+            const uint32_t v = tid < (uint32_t)kBsRadix ? S.tile_count[tid] : 0u;
+            const uint32_t ex = block_exclusive_scan<THREADS>(v, S.scan, &total);
+            if (tid < (uint32_t)kBsRadix) S.tile_start[tid] = ex;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if (dig[i] < (uint32_t)kBsRadix) {
+                const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
+                S.keys[lp] = key[i];
+                if constexpr (VALS) S.vals[lp] = val[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint32_t p = wbase + 32 * i + lane;
+            if (p < m) {
+                key[i] = S.keys[p];
+                if constexpr (VALS) val[i] = S.vals[p];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) {
+            keys_out[p] = key[i];
+            if constexpr (VALS) vals_out[p] = val[i];
+        }
+    }
+}
+
+}  // namespace ahs

@@ -1,0 +1,190 @@
+// Counting sort, keys only (Listing 2): Count[i] is the exact histogram the
+// feature pass already built (bins are values when k <= 2^16), its exclusive
+// prefix sum gives each value's first output position, and the output is
+// written run by run.  The keys are not read again: value min + j fills
+// positions [prefix[j], prefix[j+1]).  Output order for keys only is unique,
+// so the stable reverse scan of Listing 2 and this fill give the same array.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace ahs {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kFillThreads = 256;
+constexpr int kFillUnroll = 4;
+
+// Exclusive prefix of the nbins exact counts; prefix[nbins] = n.
+__global__ void __launch_bounds__(kScanThreads)
+counting_prefix(const unsigned long long* __restrict__ hist, uint32_t nb,
+                unsigned long long* __restrict__ prefix) {
+    constexpr uint32_t kPer = kMaxBins / kScanThreads;   // 64 bins per thread
+    const uint32_t j0 = threadIdx.x * kPer;
+    unsigned long long loc = 0;
+    for (uint32_t j = j0; j < j0 + kPer && j < nb; ++j) loc += hist[j];
+    __shared__ unsigned long long scratch[kScanThreads / 32 + 1];
+    unsigned long long total;
+    unsigned long long run = block_exclusive_scan<kScanThreads>(loc, scratch, &total);
+    for (uint32_t j = j0; j < j0 + kPer && j < nb; ++j) {
+        prefix[j] = run;
+        run += hist[j];
+    }
+    if (threadIdx.x == 0) prefix[nb] = total;
+}
+
+// Largest j in [lo, hi] with prefix[j] <= p (the bin holding output position p).
+__device__ __forceinline__ uint32_t bin_of(const unsigned long long* __restrict__ prefix,
+                                           uint64_t p, uint32_t lo, uint32_t hi) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kFillThreads)
+counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
+              const unsigned long long* __restrict__ prefix, uint32_t nb, K mn, K flip) {
+    constexpr int V = Vec16<K>::kN;
+    constexpr uint64_t kChunk = (uint64_t)kFillThreads * kFillUnroll;   // vectors
+    if (blockIdx.x == 0) {
+        const uint64_t tail0 = head + nvec * V;
+        if (threadIdx.x < head)
+            out[threadIdx.x] = (K)(mn + bin_of(prefix, threadIdx.x, 0, nb - 1)) ^ flip;
+        if (threadIdx.x < n - tail0) {
+            const uint64_t p = tail0 + threadIdx.x;
+            out[p] = (K)(mn + bin_of(prefix, p, 0, nb - 1)) ^ flip;
+        }
+    }
+    __shared__ uint32_t s_lo, s_hi;
+    K* body = out + head;
+    const uint64_t nchunks = ceil_div(nvec, kChunk);
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const uint64_t p0 = head + c * kChunk * V;
+            uint64_t vend = (c + 1) * kChunk;
+            vend = vend < nvec ? vend : nvec;
+            const uint64_t p1 = head + vend * V - 1;
+            s_lo = bin_of(prefix, p0, 0, nb - 1);
+            s_hi = bin_of(prefix, p1, s_lo, nb - 1);
+        }
+        __syncthreads();
+        const uint32_t lo = s_lo, hi = s_hi;
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kFillUnroll; ++u) {
+            const uint64_t v = c * kChunk + (uint64_t)u * kFillThreads + threadIdx.x;
+            if (v >= nvec) continue;
+            const uint64_t p = head + v * V;
+            uint32_t j = bin_of(prefix, p, lo, hi);
+            Vec16<K> r;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                while (prefix[j + 1] <= p + e) ++j;
+                r.e[e] = (K)(mn + (K)j) ^ flip;
+            }
+            if constexpr (sizeof(K) == 4) __stcs(reinterpret_cast<uint4*>(body + v * V), r.v);
+            else __stcs(reinterpret_cast<ulonglong2*>(body + v * V), r.v);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+copy32_vec(uint4* __restrict__ dst, const uint4* __restrict__ src, uint64_t nvec) {
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+    for (; i + 3 * stride < nvec; i += 4 * stride) {
+        const uint4 a = __ldcs(src + i), b = __ldcs(src + i + stride);
+        const uint4 c = __ldcs(src + i + 2 * stride), d = __ldcs(src + i + 3 * stride);
+        __stcs(dst + i, a);
+        __stcs(dst + i + stride, b);
+        __stcs(dst + i + 2 * stride, c);
+        __stcs(dst + i + 3 * stride, d);
+    }
+    for (; i < nvec; i += stride) __stcs(dst + i, __ldcs(src + i));
+}
+
+__global__ void __launch_bounds__(256)
+copy32_scalar(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint64_t words) {
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < words; i += stride)
+        dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(256)
+zero32_vec(uint4* __restrict__ dst, uint64_t nvec) {
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < nvec; i += stride)
+        dst[i] = make_uint4(0, 0, 0, 0);
+}
+
+uint32_t grid_for(uint64_t items, uint32_t per_block, int sms, uint32_t per_sm) {
+    uint64_t b = ceil_div(items ? items : 1, per_block);
+    const uint64_t cap = (uint64_t)sms * per_sm;
+    return (uint32_t)(b < cap ? b : cap);
+}
+
+template <typename K>
+cudaError_t fill_t(void* out_v, uint64_t n, K flip, const unsigned long long* hist,
+                   unsigned long long* prefix, K mn, uint32_t nb, int sms, cudaStream_t st) {
+    K* out = static_cast<K*>(out_v);
+    constexpr int V = Vec16<K>::kN;
+    {
+        TraceScope ts("counting_prefix", 0, st);
+        counting_prefix<<<1, kScanThreads, 0, st>>>(hist, nb, prefix);
+    }
+    const uint64_t head = head_elems<K>(out, n);
+    const uint64_t nvec = (n - head) / V;
+    const uint32_t g = grid_for(ceil_div(nvec, (uint64_t)kFillThreads * kFillUnroll), 1, sms, 8);
+    TraceScope ts("counting_fill", n, st);
+    counting_fill<K><<<g, kFillThreads, 0, st>>>(out, n, head, nvec, prefix, nb, mn, flip);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFeatures*,
+                                 const unsigned long long* hist, unsigned long long* prefix,
+                                 uint64_t min_ord, uint32_t nbins, int sms, cudaStream_t st) {
+    if (kd.bytes == 4)
+        return fill_t<uint32_t>(out, n, (uint32_t)kd.flip, hist, prefix, (uint32_t)min_ord, nbins,
+                                sms, st);
+    return fill_t<uint64_t>(out, n, kd.flip, hist, prefix, min_ord, nbins, sms, st);
+}
+
+cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st) {
+    if (words == 0 || dst == src) return cudaSuccess;
+    TraceScope ts("copy", words, st);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst), b = reinterpret_cast<uintptr_t>(src);
+    if (((a ^ b) & 15u) == 0) {
+        const uint64_t head = head_elems<uint32_t>(src, words);
+        const uint64_t nvec = (words - head) / 4;
+        const uint64_t tail = words - head - nvec * 4;
+        if (head) copy32_scalar<<<1, 256, 0, st>>>((uint32_t*)dst, (const uint32_t*)src, head);
+        if (nvec)
+            copy32_vec<<<grid_for(nvec, 1024, sms, 8), 256, 0, st>>>(
+                reinterpret_cast<uint4*>((uint32_t*)dst + head),
+                reinterpret_cast<const uint4*>((const uint32_t*)src + head), nvec);
+        if (tail)
+            copy32_scalar<<<1, 256, 0, st>>>((uint32_t*)dst + head + nvec * 4,
+                                             (const uint32_t*)src + head + nvec * 4, tail);
+    } else {
+        copy32_scalar<<<grid_for(words, 1024, sms, 8), 256, 0, st>>>((uint32_t*)dst,
+                                                                    (const uint32_t*)src, words);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero32(void* dst, uint64_t words, int sms, cudaStream_t st) {
+    if (words == 0) return cudaSuccess;
+    TraceScope ts("zero", words, st);
+    // Workspace regions are 256-byte aligned and sized in whole vectors.
+    const uint64_t nvec = ceil_div(words, 4);
+    zero32_vec<<<grid_for(nvec, 1024, sms, 8), 256, 0, st>>>(reinterpret_cast<uint4*>(dst), nvec);
+    return cudaGetLastError();
+}
+
+}  // namespace ahs

@@ -1,0 +1,77 @@
+// The library context (opaque to callers as ahs_ctx).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "select.h"
+#include "trace.h"
+
+namespace ahs {
+struct ServeState;   // serve.cpp
+}
+
+struct ahs_ctx {
+    int device = 0;
+    int sms = 152;   // replaced by the device's SM count at creation
+    ahs_config_t cfg{};
+    ahs_thresholds_t custom{};
+
+    // Persistent device block: feature record + error word (zeroed at create).
+    ahs::DevFeatures* d_rec = nullptr;
+    uint32_t* d_err = nullptr;
+    // Pinned host mirror of the persistent block.
+    ahs::DevFeatures* h_rec = nullptr;
+    uint32_t* h_err = nullptr;
+
+    // Growable device workspace.
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // Growable auxiliary device buffer (work lists) and pinned host staging.
+    void* aux = nullptr;
+    size_t aux_bytes = 0;
+    void* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::string last_cuda_error;
+    ahs::TreeModel model;
+    ahs::Tracer tracer;
+
+    ahs::ServeState* serve = nullptr;   // owned; released by ahs_serve_stop
+};
+
+namespace ahs {
+
+// Grow the workspace to at least `bytes` (synchronises the device when it
+// reallocates).  Returns AHS_ERR_OOM beyond cfg.workspace_limit or on failure.
+ahs_status ensure_workspace(ahs_ctx* ctx, size_t bytes);
+ahs_status cuda_status(ahs_ctx* ctx, cudaError_t e);
+// Features into ctx->h_rec (synchronises the stream); scratch at ctx->ws.
+ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
+                        cudaStream_t st, ahs_features_t* out);
+void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out);
+ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload);
+// Run one strategy on device-resident inputs whose features are in ctx->d_rec
+// and whose feature scratch (histogram) is at the start of ctx->ws.
+ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kout,
+                        const uint32_t* vin, uint32_t* vout, uint64_t n, KeyDesc kd,
+                        const ahs_features_t& f, cudaStream_t st, uint32_t* passes,
+                        uint32_t* buckets);
+size_t features_region(int sms);
+ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st);
+// Grow the auxiliary device buffer / pinned host staging (may synchronise).
+ahs_status ensure_aux(ahs_ctx* ctx, size_t bytes);
+ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes);
+// General path: stable sample sort with shared-memory bucket sorts.  scratch is
+// samplesort_scratch_bytes() of workspace.  Synchronises `st` once per level.
+ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
+                          uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
+                          uint32_t* levels_out, uint32_t* buckets_out);
+
+}  // namespace ahs

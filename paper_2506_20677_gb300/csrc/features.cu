@@ -1,0 +1,358 @@
+// Feature extraction: the state vector v = (n, k, H) of Section III-A.
+//
+//  K1  k1_minmax_descents  one read of the keys: min / max of the order-
+//                          preserving image, and the count of descents
+//                          (key[i] > key[i+1]); last block reduces the
+//                          per-block partials and fixes the histogram binning.
+//  K2  k2_histogram        one read of the keys: c_j = #{x : (ord(x)-min) >> s == j}
+//                          in shared memory (<= 2^16 bins), one CTA per SM,
+//                          flushed to a per-CTA slab in global memory.
+//  K3  k3_entropy          sums the slabs into the exact u64 histogram and
+//                          reduces H = -sum_j (c_j/n) log2(c_j/n) in fp64.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace ahs {
+namespace {
+
+constexpr int kK1Threads = 512;
+constexpr int kK1Unroll = 4;
+constexpr int kK2Unroll = 4;
+constexpr uint32_t kCounterBits = 21;                       // packed shared-memory counters
+constexpr unsigned long long kCounterMask = (1ull << kCounterBits) - 1;
+constexpr uint32_t kPackedWords = kHistSmemBytes / 8;       // 21,846 words, 3 counters each
+constexpr uint32_t kU32Bins = kHistSmemBytes / 4;           // bins that fit as u32 counters
+
+template <typename K>
+__device__ __forceinline__ void k1_scalar(const K* keys, uint64_t i, uint64_t n, K flip, K& mn,
+                                          K& mx, unsigned long long& desc) {
+    const K o = keys[i] ^ flip;
+    mn = o < mn ? o : mn;
+    mx = o > mx ? o : mx;
+    if (i + 1 < n) desc += (o > (K)(keys[i + 1] ^ flip)) ? 1ull : 0ull;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kK1Threads)
+k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
+                   unsigned long long* __restrict__ partials, DevFeatures* __restrict__ rec) {
+    constexpr int V = Vec16<K>::kN;
+    K mn = ~K(0), mx = 0;
+    unsigned long long desc = 0;
+    const uint32_t lane = lane_id();
+    const uint64_t gtid = (uint64_t)blockIdx.x * kK1Threads + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * kK1Threads;
+
+    // Elements before the first 16-byte boundary, and after the last full vector.
+    const uint64_t tail0 = head + nvec * V;
+    if (gtid < head) k1_scalar(keys, gtid, n, flip, mn, mx, desc);
+    if (gtid < n - tail0) k1_scalar(keys, tail0 + gtid, n, flip, mn, mx, desc);
+
+    // Vector body; lanes of a warp hold consecutive vectors, so the pair that
+    // straddles two vectors is closed with a shuffle (lane 31 loads it).
+    const K* body = keys + head;
+    for (uint64_t wb = gtid - lane; wb < nvec; wb += stride * kK1Unroll) {
+        Vec16<K> x[kK1Unroll];
+        bool ok[kK1Unroll];
+#pragma unroll
+        for (int u = 0; u < kK1Unroll; ++u) {
+            const uint64_t v = wb + lane + (uint64_t)u * stride;
+            ok[u] = v < nvec;
+            if (ok[u]) x[u] = load_vec16_stream(body + v * V);
+        }
+#pragma unroll
+        for (int u = 0; u < kK1Unroll; ++u) {
+            const uint64_t v = wb + lane + (uint64_t)u * stride;
+            const K first = ok[u] ? (K)(x[u].e[0] ^ flip) : K(0);
+            const K nxt = __shfl_down_sync(AHS_FULL_MASK, first, 1);
+            if (ok[u]) {
+                K o[V];
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    o[j] = x[u].e[j] ^ flip;
+                    mn = o[j] < mn ? o[j] : mn;
+                    mx = o[j] > mx ? o[j] : mx;
+                }
+#pragma unroll
+                for (int j = 0; j + 1 < V; ++j) desc += (o[j] > o[j + 1]) ? 1ull : 0ull;
+                const uint64_t e_next = head + (v + 1) * V;
+                if (e_next < n) {
+                    const K on = (lane < 31 && v + 1 < nvec) ? nxt : (K)(keys[e_next] ^ flip);
+                    desc += (o[V - 1] > on) ? 1ull : 0ull;
+                }
+            }
+        }
+    }
+
+    // Block reduction.
+    __shared__ unsigned long long s_min[kK1Threads / 32], s_max[kK1Threads / 32],
+        s_desc[kK1Threads / 32];
+    __shared__ bool s_last;
+    unsigned long long bmn = warp_min((unsigned long long)mn);
+    unsigned long long bmx = warp_max((unsigned long long)mx);
+    unsigned long long bd = warp_sum(desc);
+    const uint32_t warp = threadIdx.x >> 5;
+    if (lane == 0) { s_min[warp] = bmn; s_max[warp] = bmx; s_desc[warp] = bd; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kK1Threads / 32; ++w) {
+            bmn = s_min[w] < bmn ? s_min[w] : bmn;
+            bmx = s_max[w] > bmx ? s_max[w] : bmx;
+            bd += s_desc[w];
+        }
+        partials[3 * blockIdx.x + 0] = bmn;
+        partials[3 * blockIdx.x + 1] = bmx;
+        partials[3 * blockIdx.x + 2] = bd;
+        __threadfence();
+        const uint32_t ticket = atomicAdd(&rec->k1_done, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // Last block: combine all blocks and fix the binning (Section III-A reading:
+    // s = max(0, bitlen(span) - 16), nbins = (span >> s) + 1).
+    unsigned long long gmn = ~0ull, gmx = 0, gd = 0;
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += kK1Threads) {
+        const unsigned long long a = __ldcg(partials + 3 * b + 0);
+        const unsigned long long c = __ldcg(partials + 3 * b + 1);
+        gmn = a < gmn ? a : gmn;
+        gmx = c > gmx ? c : gmx;
+        gd += __ldcg(partials + 3 * b + 2);
+    }
+    gmn = warp_min(gmn);
+    gmx = warp_max(gmx);
+    gd = warp_sum(gd);
+    if (lane == 0) { s_min[warp] = gmn; s_max[warp] = gmx; s_desc[warp] = gd; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kK1Threads / 32; ++w) {
+            gmn = s_min[w] < gmn ? s_min[w] : gmn;
+            gmx = s_max[w] > gmx ? s_max[w] : gmx;
+            gd += s_desc[w];
+        }
+        const unsigned long long span = gmx - gmn;
+        const uint32_t bl = bitlen64(span);
+        const uint32_t s = bl > 16 ? bl - 16 : 0;
+        rec->min_ord = gmn;
+        rec->max_ord = gmx;
+        rec->descents = gd;
+        rec->n = n;
+        rec->span = span;
+        rec->shift = s;
+        rec->nbins = (uint32_t)((span >> s) + 1);
+        rec->k1_done = 0;
+    }
+}
+
+// Per-CTA shared histogram.  PACKED: 65,536 bins as 21-bit counters, three per
+// 64-bit word (174,768 bytes); a CTA flushes before any counter can reach 2^21.
+// Otherwise: u32 counters, replicated R times (warp w uses copy w % R) to
+// spread same-bin atomics of skewed inputs.
+template <typename K, bool PACKED>
+__device__ __forceinline__ void k2_body(const K* __restrict__ keys, uint64_t n, K flip,
+                                        uint64_t head, uint64_t nvec, K mn, uint32_t s,
+                                        uint32_t nb, uint32_t R, uint32_t* __restrict__ slabs,
+                                        unsigned long long* sm64) {
+    constexpr int V = Vec16<K>::kN;
+    constexpr uint64_t kChunkVecs = (uint64_t)kHistThreads * kK2Unroll;
+    // Chunks per epoch: keep every packed counter below 2^21 (with margin for
+    // the <= 2V scalar head/tail keys counted by CTA 0).
+    constexpr uint32_t kEpochChunks = (uint32_t)(((1u << kCounterBits) - 1 - 2 * V) / (kChunkVecs * V));
+    uint32_t* sm32 = reinterpret_cast<uint32_t*>(sm64);
+    const uint32_t warp = threadIdx.x >> 5;
+    uint32_t* mine = sm32 + (warp % R) * nb;
+
+    auto add = [&](K x) {
+        const uint32_t bin = (uint32_t)(((K)(x ^ flip) - mn) >> s);
+        if constexpr (PACKED) atomicAdd(&sm64[bin / 3], 1ull << (kCounterBits * (bin % 3)));
+        else atomicAdd(&mine[bin], 1u);
+    };
+    auto clear = [&]() {
+        if constexpr (PACKED) {
+            for (uint32_t i = threadIdx.x; i < kPackedWords; i += kHistThreads) sm64[i] = 0;
+        } else {
+            for (uint32_t i = threadIdx.x; i < R * nb; i += kHistThreads) sm32[i] = 0;
+        }
+    };
+    uint32_t* slab = slabs + (size_t)blockIdx.x * kMaxBins;
+    auto flush = [&](bool first) {
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nb; j += kHistThreads) {
+            uint32_t c;
+            if constexpr (PACKED) {
+                c = (uint32_t)((sm64[j / 3] >> (kCounterBits * (j % 3))) & kCounterMask);
+            } else {
+                c = 0;
+                for (uint32_t r = 0; r < R; ++r) c += sm32[r * nb + j];
+            }
+            slab[j] = first ? c : slab[j] + c;
+        }
+        __syncthreads();
+    };
+
+    clear();
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        const uint64_t tail0 = head + nvec * V;
+        if (threadIdx.x < head) add(keys[threadIdx.x]);
+        if (threadIdx.x < n - tail0) add(keys[tail0 + threadIdx.x]);
+    }
+    const K* body = keys + head;
+    const uint64_t nchunks = ceil_div(nvec, kChunkVecs);
+    bool first = true;
+    uint32_t in_epoch = 0;
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        Vec16<K> x[kK2Unroll];
+        bool ok[kK2Unroll];
+#pragma unroll
+        for (int u = 0; u < kK2Unroll; ++u) {
+            const uint64_t v = c * kChunkVecs + (uint64_t)u * kHistThreads + threadIdx.x;
+            ok[u] = v < nvec;
+            if (ok[u]) x[u] = load_vec16_stream(body + v * V);
+        }
+#pragma unroll
+        for (int u = 0; u < kK2Unroll; ++u)
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) add(x[u].e[j]);
+            }
+        if (PACKED && ++in_epoch == kEpochChunks) {
+            flush(first);
+            first = false;
+            in_epoch = 0;
+            clear();
+            __syncthreads();
+        }
+    }
+    flush(first);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kHistThreads, 1)
+k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
+             const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs) {
+    extern __shared__ __align__(16) unsigned long long sm64[];
+    const K mn = (K)rec->min_ord;
+    const uint32_t s = rec->shift;
+    const uint32_t nb = rec->nbins;
+    if (nb > kU32Bins) {
+        k2_body<K, true>(keys, n, flip, head, nvec, mn, s, nb, 1, slabs, sm64);
+    } else {
+        uint32_t R = kU32Bins / nb;
+        R = R > 32 ? 32 : R;
+        k2_body<K, false>(keys, n, flip, head, nvec, mn, s, nb, R, slabs, sm64);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k3_entropy(const uint32_t* __restrict__ slabs, uint32_t nslabs, uint64_t n,
+           DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
+           double* __restrict__ partials) {
+    const uint32_t nb = rec->nbins;
+    const uint32_t j = blockIdx.x * 256 + threadIdx.x;
+    double term = 0.0;
+    if (j < nb) {
+        unsigned long long tot = 0;
+        uint32_t c = 0;
+        for (; c + 4 <= nslabs; c += 4) {
+            const uint32_t a0 = slabs[(size_t)(c + 0) * kMaxBins + j];
+            const uint32_t a1 = slabs[(size_t)(c + 1) * kMaxBins + j];
+            const uint32_t a2 = slabs[(size_t)(c + 2) * kMaxBins + j];
+            const uint32_t a3 = slabs[(size_t)(c + 3) * kMaxBins + j];
+            tot += (unsigned long long)a0 + a1 + a2 + a3;
+        }
+        for (; c < nslabs; ++c) tot += slabs[(size_t)c * kMaxBins + j];
+        hist[j] = tot;
+        if (tot) {
+            const double p = (double)tot / (double)n;
+            term = -p * log2(p);
+        }
+    }
+    __shared__ double s_part[8];
+    __shared__ bool s_last;
+    term = warp_sum(term);
+    if (lane_id() == 0) s_part[threadIdx.x >> 5] = term;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < 8; ++w) b += s_part[w];
+        partials[blockIdx.x] = b;
+        __threadfence();
+        s_last = (atomicAdd(&rec->k3_done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    double H = 0.0;
+    for (uint32_t b = 0; b < gridDim.x; ++b) H += __ldcg(partials + b);
+    rec->entropy = H;
+    rec->entropy_norm = nb > 1 ? H / log2((double)nb) : 0.0;
+    rec->k3_done = 0;
+}
+
+template <typename K>
+cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScratch& s, int sms,
+                       cudaStream_t st) {
+    const K* keys = static_cast<const K*>(keys_v);
+    constexpr int V = Vec16<K>::kN;
+    const uint64_t head = head_elems<K>(keys, n);
+    const uint64_t nvec = (n - head) / V;
+    const uint32_t g1 = k1_blocks(n, sms);
+    {
+        TraceScope ts("features_minmax", n, st);
+        k1_minmax_descents<K><<<g1, kK1Threads, 0, st>>>(keys, n, flip, head, nvec, s.k1_partials,
+                                                          s.rec);
+    }
+    const uint32_t g2 = (uint32_t)sms;
+    {
+        TraceScope ts("features_histogram", n, st);
+        k2_histogram<K><<<g2, kHistThreads, kHistSmemBytes, st>>>(keys, n, flip, head, nvec, s.rec,
+                                                                  s.slabs);
+    }
+    {
+        TraceScope ts("features_entropy", 0, st);
+        k3_entropy<<<kEntropyBlocks, 256, 0, st>>>(s.slabs, g2, n, s.rec, s.hist, s.ent_partials);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t k1_blocks(uint64_t n, int sms) {
+    const uint64_t per = (uint64_t)kK1Threads * kK1Unroll * 4;
+    uint64_t b = ceil_div(n ? n : 1, per);
+    const uint64_t cap = 4ull * (uint64_t)sms;
+    return (uint32_t)(b < cap ? b : cap);
+}
+
+size_t features_scratch_bytes(int sms) {
+    return 3 * sizeof(unsigned long long) * 4 * (size_t)sms + 256 +
+           (size_t)sms * kMaxBins * sizeof(uint32_t) + 256 +
+           kMaxBins * sizeof(unsigned long long) + 256 + kEntropyBlocks * sizeof(double) + 256;
+}
+
+cudaError_t launch_features(const void* keys, uint64_t n, KeyDesc kd, const FeatureScratch& s,
+                            int sms, cudaStream_t st) {
+    static bool attr_set[2] = {false, false};
+    if (kd.bytes == 4) {
+        if (!attr_set[0]) {
+            cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint32_t>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kHistSmemBytes);
+            if (e != cudaSuccess) return e;
+            attr_set[0] = true;
+        }
+        return features_t<uint32_t>(keys, n, (uint32_t)kd.flip, s, sms, st);
+    }
+    if (!attr_set[1]) {
+        cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint64_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kHistSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set[1] = true;
+    }
+    return features_t<uint64_t>(keys, n, kd.flip, s, sms, st);
+}
+
+}  // namespace ahs

@@ -1,0 +1,106 @@
+// Internal (non-ABI) declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ahs.h"
+
+namespace ahs {
+
+// Device-resident feature record, written by the feature kernels and copied to
+// the host in one piece.  Self-resetting block counters live here too.
+struct DevFeatures {
+    unsigned long long min_ord;   // order-preserving image of the smallest key
+    unsigned long long max_ord;
+    unsigned long long descents;
+    unsigned long long n;
+    unsigned long long span;
+    uint32_t shift;
+    uint32_t nbins;
+    double entropy;
+    double entropy_norm;
+    uint32_t k1_done;             // last-block counters (return to 0 after each use)
+    uint32_t k3_done;
+    uint32_t rh_done;             // radix digit-histogram kernel
+    uint32_t pad0;
+    unsigned long long pad[6];
+};
+static_assert(sizeof(DevFeatures) == 128, "DevFeatures layout");
+
+constexpr uint32_t kMaxBins = 1u << 16;             // histogram bins, Section III-A reading
+constexpr uint32_t kHistSmemBytes = 21846u * 8u;    // 65,536 21-bit counters, 3 per u64 word
+constexpr uint32_t kHistThreads = 1024;
+constexpr uint32_t kEntropyBlocks = kMaxBins / 256;
+
+// Key type descriptors.
+struct KeyDesc {
+    uint32_t bytes;      // 4 or 8
+    uint64_t flip;       // sign bit for signed types
+};
+inline KeyDesc key_desc(ahs_key_type t) {
+    switch (t) {
+    case AHS_U32: return {4, 0};
+    case AHS_I32: return {4, 0x80000000ull};
+    case AHS_U64: return {8, 0};
+    default: return {8, 0x8000000000000000ull};
+    }
+}
+
+// ------------------------------------------------------------------ features
+struct FeatureScratch {
+    DevFeatures* rec;                 // persistent, zero-initialised
+    unsigned long long* k1_partials;  // 3 per K1 block
+    uint32_t* slabs;                  // hist_blocks x kMaxBins
+    unsigned long long* hist;         // kMaxBins exact counts (u64)
+    double* ent_partials;             // kEntropyBlocks
+};
+uint32_t k1_blocks(uint64_t n, int sms);
+size_t features_scratch_bytes(int sms);
+cudaError_t launch_features(const void* keys, uint64_t n, KeyDesc kd, const FeatureScratch& s,
+                            int sms, cudaStream_t st);
+
+// ------------------------------------------------------------------ counting
+// Keys-only counting sort (Listing 2) from the exact histogram of the feature
+// pass (requires hist_shift == 0).  prefix: kMaxBins + 1 u64 of scratch.
+cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFeatures* rec,
+                                 const unsigned long long* hist, unsigned long long* prefix,
+                                 uint64_t min_ord, uint32_t nbins, int sms, cudaStream_t st);
+
+// Copy `words` 32-bit words (keys or payload) from src to dst.
+cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st);
+// Zero `words` 32-bit words.
+cudaError_t launch_zero32(void* dst, uint64_t words, int sms, cudaStream_t st);
+
+// --------------------------------------------------------------------- radix
+struct RadixPlan {
+    uint32_t passes;
+    uint32_t shift[8];   // low bit of each pass's digit
+    uint32_t bits[8];    // digit width of each pass (<= 8)
+};
+RadixPlan radix_plan(uint64_t span);
+size_t radix_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes);
+struct RadixScratch {
+    void* keys_tmp;                   // n keys
+    uint32_t* vals_tmp;               // n payload words (or null)
+    unsigned long long* digit_hist;   // 8 x 256 (u64)
+    uint32_t* status;                 // passes x tiles x 256 look-back words
+    uint32_t* tile_counters;          // 8
+    uint64_t tiles;
+};
+RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes);
+// Stable LSD radix sort over ord(x) - min (onesweep passes with decoupled look-back).
+cudaError_t launch_radix_sort(const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                              uint32_t* vals_out, uint64_t n, KeyDesc kd, uint64_t min_ord,
+                              const RadixPlan& plan, const RadixScratch& rs, DevFeatures* rec,
+                              uint32_t* err, int sms, cudaStream_t st);
+
+// ------------------------------------------------------- one-block sort (SMALL)
+uint64_t blocksort_capacity(uint32_t key_bytes, bool has_vals);
+cudaError_t launch_blocksort_single(const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                    uint32_t* vals_out, uint64_t n, KeyDesc kd, cudaStream_t st);
+
+// ------------------------------------------------------ general: sample sort
+size_t samplesort_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals);
+
+}  // namespace ahs

@@ -1,0 +1,398 @@
+// LSD radix sort (Listing 3, Section III-G) over u = ord(x) - min.
+//
+// The paper distributes keys into base-b buckets digit by digit, least
+// significant first, appending in input order (stable), with d = ceil(log_b k)
+// passes (Eq. 4).  Here b = 2^8 and each pass is one "onesweep" kernel: a tile
+// of keys is ranked by digit in shared memory (warp match + cross-warp scan),
+// the tile's per-digit counts are published and the exclusive prefix over all
+// earlier tiles is found by decoupled look-back (Merrill & Garland 2016;
+// one-sweep formulation of Adinets & Merrill 2022), and the tile is staged in
+// shared memory in digit order so every digit's run is written contiguously.
+// The global digit offsets of all passes come from one histogram kernel that
+// reads the keys once before the first pass.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace ahs {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagIncl = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;     // ~1 s with the backoff below
+
+constexpr int kHistThreadsR = 512;
+constexpr int kHistReplicas = 4;
+
+struct PassDesc {
+    uint32_t passes;
+    uint32_t shift[8];
+    uint32_t bits[8];
+};
+
+// Histogram of every pass's digit in one read (dhist zeroed beforehand); the
+// last block turns the counts into per-pass exclusive digit offsets.
+template <typename K>
+__global__ void __launch_bounds__(kHistThreadsR)
+radix_digit_hist(const K* __restrict__ keys, uint64_t n, K mn, K flip, uint64_t head,
+                 uint64_t nvec, PassDesc pd, unsigned long long* __restrict__ dhist,
+                 uint32_t* __restrict__ dbase, DevFeatures* __restrict__ rec) {
+    constexpr int V = Vec16<K>::kN;
+    __shared__ uint32_t sh[kHistReplicas][8][kRadix];
+    __shared__ bool s_last;
+    const uint32_t P = pd.passes;
+    for (uint32_t i = threadIdx.x; i < kHistReplicas * 8 * kRadix; i += kHistThreadsR)
+        (&sh[0][0][0])[i] = 0;
+    __syncthreads();
+    uint32_t(*mine)[kRadix] = sh[(threadIdx.x >> 5) % kHistReplicas];
+    auto add = [&](K x) {
+        const K u = (K)(x ^ flip) - mn;
+        for (uint32_t p = 0; p < P; ++p)
+            atomicAdd(&mine[p][(uint32_t)(u >> pd.shift[p]) & ((1u << pd.bits[p]) - 1)], 1u);
+    };
+    const uint64_t gtid = (uint64_t)blockIdx.x * kHistThreadsR + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * kHistThreadsR;
+    const uint64_t tail0 = head + nvec * V;
+    if (gtid < head) add(keys[gtid]);
+    if (gtid < n - tail0) add(keys[tail0 + gtid]);
+    const K* body = keys + head;
+    for (uint64_t v = gtid; v < nvec; v += 2 * stride) {
+        Vec16<K> a = load_vec16(body + v * V);
+        const bool ok2 = v + stride < nvec;
+        Vec16<K> b;
+        if (ok2) b = load_vec16(body + (v + stride) * V);
+#pragma unroll
+        for (int j = 0; j < V; ++j) add(a.e[j]);
+        if (ok2) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) add(b.e[j]);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P * kRadix; i += kHistThreadsR) {
+        const uint32_t p = i / kRadix, d = i % kRadix;
+        uint32_t c = 0;
+#pragma unroll
+        for (int r = 0; r < kHistReplicas; ++r) c += sh[r][p][d];
+        if (c) atomicAdd(&dhist[p * kRadix + d], (unsigned long long)c);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&rec->rh_done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    // Last block: exclusive prefix per pass (one warp per pass), then clear.
+    const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+    if (warp < P) {
+        unsigned long long run = 0;
+        for (int base = 0; base < kRadix; base += 32) {
+            const unsigned long long c = atomicAdd(&dhist[warp * kRadix + base + lane], 0ull);
+            const unsigned long long inc = warp_inclusive_scan(c);
+            dbase[warp * kRadix + base + lane] = (uint32_t)(run + inc - c);
+            run += __shfl_sync(AHS_FULL_MASK, inc, 31);
+        }
+    }
+    if (threadIdx.x == 0) rec->rh_done = 0;
+}
+
+template <typename K, bool VALS, int THREADS, int IPT>
+struct OnesweepSmem {
+    static constexpr int W = THREADS / 32;
+    static constexpr int TILE = THREADS * IPT;
+    uint32_t warp_hist[W][kRadix];
+    uint32_t tile_count[kRadix];
+    uint32_t tile_start[kRadix];
+    uint32_t gbase[kRadix];
+    uint32_t scan[W + 1];
+    uint32_t tile_id;
+    K keys[TILE];
+    uint32_t vals[VALS ? TILE : 1];
+};
+
+template <typename K, bool VALS, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS)
+onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
+              const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ vals_out, uint32_t n,
+              K mn, K flip, uint32_t shift, uint32_t bits, const uint32_t* __restrict__ dbase,
+              uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+              uint32_t* __restrict__ err) {
+    using Smem = OnesweepSmem<K, VALS, THREADS, IPT>;
+    constexpr int W = Smem::W;
+    constexpr int TILE = Smem::TILE;
+    constexpr int WARP_ITEMS = 32 * IPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t mask = (1u << bits) - 1;
+
+    if (tid == 0) S.tile_id = atomicAdd(tile_counter, 1u);
+    for (uint32_t i = tid; i < W * kRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = S.tile_id;
+    const uint32_t tile_base = tile * (uint32_t)TILE;
+    const uint32_t wbase = tile_base + warp * WARP_ITEMS;
+
+    // Load warp-striped: item i of lane l is key wbase + 32 i + l.
+    K key[IPT];
+    uint32_t dig[IPT];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t idx = wbase + 32 * i + lane;
+        if (idx < n) {
+            key[i] = keys_in[idx];
+            dig[i] = (uint32_t)(((K)(key[i] ^ flip) - mn) >> shift) & mask;
+        } else {
+            key[i] = 0;
+            dig[i] = kRadix;   // past the end: ranked nowhere
+        }
+    }
+
+    // Rank within the warp in input order (stable): peers share a digit.
+    uint32_t rank[IPT];
+    uint32_t* wh = S.warp_hist[warp];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t peers = __match_any_sync(AHS_FULL_MASK, dig[i]);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && dig[i] < kRadix) old = atomicAdd(&wh[dig[i]], __popc(peers));
+        old = __shfl_sync(AHS_FULL_MASK, old, leader);
+        rank[i] = old + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // Per digit: exclusive prefix over warps and the tile's count.
+    for (uint32_t d = tid; d < kRadix; d += THREADS) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t c = S.warp_hist[w][d];
+            S.warp_hist[w][d] = run;
+            run += c;
+        }
+        S.tile_count[d] = run;
+        // Publish this tile's aggregate as early as possible.
+        st_relaxed_gpu(&status[(size_t)tile * kRadix + d], (tile == 0 ? kFlagIncl : kFlagAgg) | run);
+    }
+    __syncthreads();
+    {
+        uint32_t total;
+        const uint32_t v = tid < (uint32_t)kRadix ? S.tile_count[tid] : 0u;
+        const uint32_t ex = block_exclusive_scan<THREADS>(v, S.scan, &total);
+        if (tid < (uint32_t)kRadix) S.tile_start[tid] = ex;
+    }
+    // (block_exclusive_scan ends with __syncthreads)
+
+    // Stage the tile in digit order.
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        if (dig[i] < kRadix) {
+            const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
+            S.keys[lp] = key[i];
+        }
+    }
+    if constexpr (VALS) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint32_t idx = wbase + 32 * i + lane;
+            if (dig[i] < kRadix) {
+                const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
+                S.vals[lp] = vals_in[idx];
+            }
+        }
+    }
+
+    // Decoupled look-back: exclusive prefix of this digit over earlier tiles.
+    if (tid < (uint32_t)kRadix) {
+        const uint32_t d = tid;
+        uint32_t excl = 0;
+        if (tile > 0) {
+            int64_t j = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const uint32_t s = ld_relaxed_gpu(&status[(size_t)j * kRadix + d]);
+                const uint32_t flag = s & ~kCountMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) { report_error(err, kDevLookbackTimeout); break; }
+                    // Another tile gave up already: stop waiting too.
+                    if ((spins & 1023u) == 0 && ld_relaxed_gpu(err) != 0) break;
+                    if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
+                    continue;
+                }
+                excl += s & kCountMask;
+                if (flag == kFlagIncl) break;
+                --j;
+            }
+            st_relaxed_gpu(&status[(size_t)tile * kRadix + d], kFlagIncl | (excl + S.tile_count[d]));
+        }
+        S.gbase[d] = dbase[d] + excl - S.tile_start[d];
+    }
+    __syncthreads();
+
+    // Write the staged tile: runs of one digit go to consecutive addresses.
+    const uint32_t tile_n = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
+    for (uint32_t j = tid; j < tile_n; j += THREADS) {
+        const K k = S.keys[j];
+        const uint32_t d = (uint32_t)(((K)(k ^ flip) - mn) >> shift) & mask;
+        const uint32_t gp = S.gbase[d] + j;
+        if (gp >= n) { report_error(err, kDevBadState); continue; }   // only after a failed wait
+        keys_out[gp] = k;
+        if constexpr (VALS) vals_out[gp] = S.vals[j];
+    }
+}
+
+template <typename K, bool VALS>
+struct OnesweepCfg;
+template <> struct OnesweepCfg<uint32_t, false> { static constexpr int T = 512, IPT = 16; };
+template <> struct OnesweepCfg<uint32_t, true> { static constexpr int T = 512, IPT = 12; };
+template <> struct OnesweepCfg<uint64_t, false> { static constexpr int T = 512, IPT = 12; };
+template <> struct OnesweepCfg<uint64_t, true> { static constexpr int T = 512, IPT = 8; };
+
+template <typename K, bool VALS>
+constexpr int tile_keys() { return OnesweepCfg<K, VALS>::T * OnesweepCfg<K, VALS>::IPT; }
+
+template <typename K, bool VALS>
+cudaError_t radix_t(const void* kin_v, void* kout_v, const uint32_t* vin, uint32_t* vout,
+                    uint64_t n, K flip, K mn, const RadixPlan& plan, const RadixScratch& rs,
+                    DevFeatures* rec, uint32_t* err, int sms, cudaStream_t st) {
+    constexpr int T = OnesweepCfg<K, VALS>::T, IPT = OnesweepCfg<K, VALS>::IPT;
+    constexpr int TILE = T * IPT;
+    using Smem = OnesweepSmem<K, VALS, T, IPT>;
+    const K* kin = static_cast<const K*>(kin_v);
+    K* kout = static_cast<K*>(kout_v);
+    K* ktmp = static_cast<K*>(rs.keys_tmp);
+    const uint32_t P = plan.passes;
+    const uint64_t tiles = ceil_div(n, TILE);
+    cudaError_t e;
+
+    // Histogram of all passes' digits, and their exclusive offsets.
+    PassDesc pd{};
+    pd.passes = P;
+    for (uint32_t p = 0; p < P; ++p) { pd.shift[p] = plan.shift[p]; pd.bits[p] = plan.bits[p]; }
+    uint32_t* dbase = reinterpret_cast<uint32_t*>(rs.digit_hist + 8 * kRadix);
+    // One zeroing launch covers the digit counts, the look-back status words
+    // of every pass and the tile counters (carved contiguously).
+    {
+        const uint64_t words = (uint64_t)(rs.tile_counters + 8 - reinterpret_cast<uint32_t*>(rs.digit_hist));
+        e = launch_zero32(rs.digit_hist, words, sms, st);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        constexpr int V = Vec16<K>::kN;
+        const uint64_t head = head_elems<K>(kin, n);
+        const uint64_t nvec = (n - head) / V;
+        uint64_t g = ceil_div(nvec ? nvec : 1, (uint64_t)kHistThreadsR * 4);
+        const uint64_t cap = 2ull * sms;
+        g = g < cap ? g : cap;
+        TraceScope ts("radix_digit_hist", n, st);
+        radix_digit_hist<K><<<(uint32_t)g, kHistThreadsR, 0, st>>>(
+            kin, n, mn, flip, head, nvec, pd, rs.digit_hist, dbase, rec);
+    }
+
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(onesweep_pass<K, VALS, T, IPT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+
+    // Buffer schedule: the last pass writes kout.  When sorting in place with
+    // an odd pass count, first move the keys into the temporary buffer.
+    const bool inplace = (kin_v == kout_v);
+    const K* src = kin;
+    const uint32_t* vsrc = vin;
+    if (inplace && (P % 2 == 1)) {
+        e = launch_copy32(ktmp, kin, n * sizeof(K) / 4, sms, st);
+        if (e != cudaSuccess) return e;
+        if (VALS) {
+            e = launch_copy32(rs.vals_tmp, vin, n, sms, st);
+            if (e != cudaSuccess) return e;
+        }
+        src = ktmp;
+        vsrc = rs.vals_tmp;
+    }
+    for (uint32_t p = 0; p < P; ++p) {
+        const bool to_out = ((P - 1 - p) % 2) == 0;
+        K* dst = to_out ? kout : ktmp;
+        uint32_t* vdst = to_out ? vout : rs.vals_tmp;
+        uint32_t* status = rs.status + (size_t)p * tiles * kRadix;
+        TraceScope ts("radix_onesweep", n, st);
+        onesweep_pass<K, VALS, T, IPT><<<(uint32_t)tiles, T, sizeof(Smem), st>>>(
+            src, dst, vsrc, vdst, (uint32_t)n, mn, flip, plan.shift[p], plan.bits[p],
+            dbase + p * kRadix, status, rs.tile_counters + p, err);
+        src = dst;
+        vsrc = vdst;
+    }
+    return cudaGetLastError();
+}
+
+uint64_t tile_keys_for(uint32_t key_bytes, bool has_vals) {
+    if (key_bytes == 4) return has_vals ? tile_keys<uint32_t, true>() : tile_keys<uint32_t, false>();
+    return has_vals ? tile_keys<uint64_t, true>() : tile_keys<uint64_t, false>();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+RadixPlan radix_plan(uint64_t span) {
+    RadixPlan p{};
+    const uint32_t D = bitlen64(span);
+    p.passes = (D + 7) / 8;
+    for (uint32_t i = 0; i < p.passes; ++i) {
+        p.shift[i] = 8 * i;
+        const uint32_t hi = 8 * i + 8 < D ? 8 * i + 8 : D;
+        p.bits[i] = hi - 8 * i;
+    }
+    return p;
+}
+
+size_t radix_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes) {
+    const uint64_t tiles = ceil_div(n, tile_keys_for(key_bytes, has_vals));
+    return align256(n * key_bytes) + (has_vals ? align256(n * 4) : 0) +
+           align256(8 * kRadix * sizeof(unsigned long long) + 8 * kRadix * sizeof(uint32_t)) +
+           align256(((size_t)passes * tiles * kRadix + 8) * sizeof(uint32_t)) + 256;
+}
+
+RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_vals,
+                         uint32_t passes) {
+    RadixScratch r{};
+    char* p = static_cast<char*>(base);
+    r.tiles = ceil_div(n, tile_keys_for(key_bytes, has_vals));
+    r.keys_tmp = p;
+    p += align256(n * key_bytes);
+    if (has_vals) {
+        r.vals_tmp = reinterpret_cast<uint32_t*>(p);
+        p += align256(n * 4);
+    }
+    r.digit_hist = reinterpret_cast<unsigned long long*>(p);   // digit bases follow it
+    p += align256(8 * kRadix * sizeof(unsigned long long) + 8 * kRadix * sizeof(uint32_t));
+    r.status = reinterpret_cast<uint32_t*>(p);
+    r.tile_counters = r.status + (size_t)passes * r.tiles * kRadix;
+    return r;
+}
+
+cudaError_t launch_radix_sort(const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                              uint32_t* vals_out, uint64_t n, KeyDesc kd, uint64_t min_ord,
+                              const RadixPlan& plan, const RadixScratch& rs, DevFeatures* rec,
+                              uint32_t* err, int sms, cudaStream_t st) {
+    const bool v = vals_in != nullptr;
+    if (kd.bytes == 4) {
+        if (v) return radix_t<uint32_t, true>(keys_in, keys_out, vals_in, vals_out, n,
+                                              (uint32_t)kd.flip, (uint32_t)min_ord, plan, rs, rec,
+                                              err, sms, st);
+        return radix_t<uint32_t, false>(keys_in, keys_out, nullptr, nullptr, n, (uint32_t)kd.flip,
+                                        (uint32_t)min_ord, plan, rs, rec, err, sms, st);
+    }
+    if (v) return radix_t<uint64_t, true>(keys_in, keys_out, vals_in, vals_out, n, kd.flip,
+                                          min_ord, plan, rs, rec, err, sms, st);
+    return radix_t<uint64_t, false>(keys_in, keys_out, nullptr, nullptr, n, kd.flip, min_ord, plan,
+                                    rs, rec, err, sms, st);
+}
+
+}  // namespace ahs

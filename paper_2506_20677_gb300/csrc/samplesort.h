@@ -1,0 +1,33 @@
+// Types shared by the general path (sample sort) and the bucket sorts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace ahs {
+
+// Largest bucket one CTA sorts in shared memory, and the size classes of the
+// bucket kernels (128x8, 256x16 and 512x16 threads x keys).
+constexpr uint32_t kBucketCap = 8192;
+constexpr uint32_t kBucketClassCap[3] = {1024, 4096, 8192};
+
+// A bucket that leaves the partition levels: its keys sit in buffer `where`
+// (0: temporary, 1: the output) at [begin, begin + size).
+struct FinalBucket {
+    unsigned long long begin;
+    uint32_t size;
+    uint8_t where;
+    uint8_t sort;      // 0: all keys equal (or one key), copy only
+    uint16_t pad;
+};
+static_assert(sizeof(FinalBucket) == 16, "FinalBucket layout");
+
+uint32_t bucket_class(uint32_t size);
+cudaError_t launch_bucket_finish(const FinalBucket* d_lists[3], const uint32_t counts[3],
+                                 const uint64_t keys[3], const void* buf0, const void* buf1, void* out,
+                                 const uint32_t* vbuf0, const uint32_t* vbuf1, uint32_t* vout,
+                                 KeyDesc kd, cudaStream_t st);
+
+}  // namespace ahs
