@@ -32,11 +32,16 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
+def _flags():
+    # AHS_CHECKS=1: device self-checks (bounds checks that print and skip).
+    return NVCC_FLAGS + (["-DAHS_DEVICE_CHECKS"] if os.environ.get("AHS_CHECKS") == "1" else [])
+
+
 def _compile(src: str, verbose_ptxas: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [_nvcc(), *ARCH, *_flags(), "-c", src, "-o", obj + ".tmp"]
     if verbose_ptxas and src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

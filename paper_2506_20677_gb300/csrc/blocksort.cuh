@@ -103,19 +103,15 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
             S.tile_count[d] = run;
         }
         __syncthreads();
-        {
-            uint32_t total;
-            const uint32_t v = tid < (uint32_t)kBsRadix ? S.tile_count[tid] : 0u;
-            const uint32_t ex = block_exclusive_scan<THREADS>(v, S.scan, &total);
-            if (tid < (uint32_t)kBsRadix) S.tile_start[tid] = ex;
-        }
-        __syncthreads();
+        scan_digit_counts<THREADS, kBsRadix>(S.tile_count, S.tile_start, S.scan);
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             if (dig[i] < (uint32_t)kBsRadix) {
                 const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
-                S.keys[lp] = key[i];
-                if constexpr (VALS) S.vals[lp] = val[i];
+                if (AHS_DCHECK(lp < m, "blocksort stage", lp)) {
+                    S.keys[lp] = key[i];
+                    if constexpr (VALS) S.vals[lp] = val[i];
+                }
             }
         }
         __syncthreads();

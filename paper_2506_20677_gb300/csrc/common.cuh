@@ -6,6 +6,20 @@
 
 #define AHS_FULL_MASK 0xffffffffu
 
+// Device self-checks (build with AHS_CHECKS=1): a failed check prints the
+// site and the offending index and the access is skipped.
+#ifdef AHS_DEVICE_CHECKS
+#include <cstdio>
+#define AHS_DCHECK(cond, what, idx)                                                         \
+    ((cond) ? true                                                                          \
+            : (printf("AHS check failed: %s at %s:%d block %d thread %d idx %llu\n", what, \
+                      __FILE__, __LINE__, (int)blockIdx.x, (int)threadIdx.x,                \
+                      (unsigned long long)(idx)),                                           \
+               false))
+#else
+#define AHS_DCHECK(cond, what, idx) true
+#endif
+
 namespace ahs {
 
 // Number of SMs on the device the kernels are sized for; the host passes the
@@ -132,6 +146,41 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
     *total = scratch[W];
     __syncthreads();
     return r;
+}
+
+// Exclusive scan of NB per-digit counts with a block of BLOCK threads, for
+// any BLOCK (each thread owns NB / BLOCK consecutive digits when NB >= BLOCK).
+// start[d] = sum of count[d'] for d' < d.  Ends with __syncthreads, so start
+// is visible to the whole block on return.
+template <int BLOCK, int NB>
+__device__ __forceinline__ void scan_digit_counts(const uint32_t* count, uint32_t* start,
+                                                  uint32_t* scratch) {
+    constexpr int PER = NB >= BLOCK ? NB / BLOCK : 1;
+    static_assert(NB < BLOCK || NB % BLOCK == 0, "digit count must divide evenly");
+    const uint32_t tid = threadIdx.x;
+    uint32_t loc[PER];
+    uint32_t sum = 0;
+    if constexpr (NB >= BLOCK) {
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            loc[r] = count[tid * PER + r];
+            sum += loc[r];
+        }
+    } else {
+        sum = tid < (uint32_t)NB ? count[tid] : 0u;
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<BLOCK>(sum, scratch, &total);
+    if constexpr (NB >= BLOCK) {
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            start[tid * PER + r] = run;
+            run += loc[r];
+        }
+    } else {
+        if (tid < (uint32_t)NB) start[tid] = run;
+    }
+    __syncthreads();
 }
 
 // Relaxed GPU-scope 32-bit load/store used for look-back status words: the

@@ -83,7 +83,7 @@ counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
             Vec16<K> r;
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-                while (prefix[j + 1] <= p + e) ++j;
+                while (AHS_DCHECK(j < nb, "fill bin", j) && prefix[j + 1] <= p + e) ++j;
                 r.e[e] = (K)(mn + (K)j) ^ flip;
             }
             if constexpr (sizeof(K) == 4) __stcs(reinterpret_cast<uint4*>(body + v * V), r.v);

@@ -166,6 +166,7 @@ __device__ __forceinline__ void k2_body(const K* __restrict__ keys, uint64_t n, 
 
     auto add = [&](K x) {
         const uint32_t bin = (uint32_t)(((K)(x ^ flip) - mn) >> s);
+        if (!AHS_DCHECK(bin < nb, "k2 bin", bin)) return;
         if constexpr (PACKED) atomicAdd(&sm64[bin / 3], 1ull << (kCounterBits * (bin % 3)));
         else atomicAdd(&mine[bin], 1u);
     };

@@ -132,6 +132,7 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
     for (uint32_t i = tid; i < W * kRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = S.tile_id;
+    if (!AHS_DCHECK(tile < gridDim.x, "onesweep tile id", tile)) return;
     const uint32_t tile_base = tile * (uint32_t)TILE;
     const uint32_t wbase = tile_base + warp * WARP_ITEMS;
 
@@ -179,20 +180,14 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
         st_relaxed_gpu(&status[(size_t)tile * kRadix + d], (tile == 0 ? kFlagIncl : kFlagAgg) | run);
     }
     __syncthreads();
-    {
-        uint32_t total;
-        const uint32_t v = tid < (uint32_t)kRadix ? S.tile_count[tid] : 0u;
-        const uint32_t ex = block_exclusive_scan<THREADS>(v, S.scan, &total);
-        if (tid < (uint32_t)kRadix) S.tile_start[tid] = ex;
-    }
-    // (block_exclusive_scan ends with __syncthreads)
+    scan_digit_counts<THREADS, kRadix>(S.tile_count, S.tile_start, S.scan);
 
     // Stage the tile in digit order.
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (dig[i] < kRadix) {
             const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
-            S.keys[lp] = key[i];
+            if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep stage", lp)) S.keys[lp] = key[i];
         }
     }
     if constexpr (VALS) {
@@ -201,7 +196,7 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
             const uint32_t idx = wbase + 32 * i + lane;
             if (dig[i] < kRadix) {
                 const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
-                S.vals[lp] = vals_in[idx];
+                if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep vstage", lp)) S.vals[lp] = vals_in[idx];
             }
         }
     }

@@ -125,8 +125,10 @@ ss_count(const K* __restrict__ src, const TileDesc* __restrict__ tiles, const K*
     __syncthreads();
     const K* p = src + t.begin;
 #pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < t.size; i += kThreads)
-        atomicAdd(&hist[classify(sp, m, (K)(p[i] ^ flip))], 1u);
+    for (uint32_t i = threadIdx.x; i < t.size; i += kThreads) {
+        const uint32_t b = classify(sp, m, (K)(p[i] ^ flip));
+        if (AHS_DCHECK(b < kCols, "count bucket", b)) atomicAdd(&hist[b], 1u);
+    }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < kCols; i += kThreads)
         counts[(size_t)blockIdx.x * kCols + i] = hist[i];
@@ -250,16 +252,17 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
             run += c;
         }
         S.tile_count[j] = run;
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan<kThreads>(run, S.scan, &total);
-        S.tile_start[j] = ex;
-        S.gbase[j] = (uint32_t)(offs[(size_t)blockIdx.x * kCols + j]) - ex;
     }
+    __syncthreads();
+    scan_digit_counts<kThreads, kCols>(S.tile_count, S.tile_start, S.scan);
+    for (uint32_t j = tid; j < kCols; j += kThreads)
+        S.gbase[j] = (uint32_t)(offs[(size_t)blockIdx.x * kCols + j]) - S.tile_start[j];
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
         if (b[i] < kCols) {
             const uint32_t lp = S.tile_start[b[i]] + S.warp_hist[warp][b[i]] + rank[i];
+            if (!AHS_DCHECK(lp < t.size, "scatter stage", lp)) continue;
             S.keys[lp] = key[i];
             S.bid[lp] = (uint16_t)b[i];
         }
@@ -270,7 +273,7 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
         for (int i = 0; i < kIpt; ++i) {
             if (b[i] < kCols) {
                 const uint32_t lp = S.tile_start[b[i]] + S.warp_hist[warp][b[i]] + rank[i];
-                S.vals[lp] = vp[wbase + 32 * i + lane];
+                if (AHS_DCHECK(lp < t.size, "scatter vstage", lp)) S.vals[lp] = vp[wbase + 32 * i + lane];
             }
         }
     }

@@ -5,9 +5,21 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 namespace ahs {
+
+// AHS_DEBUG_SYNC=1 in the environment: synchronise after every traced launch
+// and name the kernel whose execution failed (debugging aid).
+inline bool debug_sync() {
+    static const bool on = [] {
+        const char* v = std::getenv("AHS_DEBUG_SYNC");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
 
 struct TraceRecord {
     const char* name;
@@ -36,7 +48,7 @@ extern thread_local Tracer* g_tracer;
 
 class TraceScope {
 public:
-    TraceScope(const char* name, uint64_t items, cudaStream_t st) : st_(st) {
+    TraceScope(const char* name, uint64_t items, cudaStream_t st) : st_(st), name_(name) {
         if (g_tracer && g_tracer->on) {
             rec_.name = name;
             rec_.items = items;
@@ -47,6 +59,11 @@ public:
         }
     }
     ~TraceScope() {
+        if (debug_sync()) {
+            cudaError_t e = cudaStreamSynchronize(st_);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) std::fprintf(stderr, "[ahs] kernel %s failed: %s\n", name_, cudaGetErrorString(e));
+        }
         if (active_) {
             cudaEventRecord(rec_.b, st_);
             g_tracer->records.push_back(rec_);
@@ -57,6 +74,7 @@ public:
 
 private:
     cudaStream_t st_;
+    const char* name_;
     TraceRecord rec_{};
     bool active_ = false;
 };
