@@ -181,6 +181,29 @@ ahs_status ahs_trace_collect(ahs_ctx* ctx, ahs_trace_entry_t* out, uint32_t cap,
 ahs_status ahs_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_type type,
                         void* stream, ahs_features_t* h_out);
 
+/* Feature extraction that allocates nothing.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc when they need the state
+ * vector (for instance while a stream is being captured into a CUDA graph,
+ * when all device memory is reserved up front by another allocator, or on a
+ * path that cannot afford the device synchronisation of cudaMalloc/cudaFree).
+ * It runs the same kernels as ahs_features and returns the same result, with
+ * no ahs_ctx.  Its scratch is one fixed 48 MiB device array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *  - d_keys: device keys on the current device; n <= AHS_NOALLOC_MAX_KEYS.
+ *  - The first call on a device resolves the array's device address for that
+ *    device; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the previous call's contents
+ *    (each call clears what must start at zero): calls that overlap on the GPU
+ *    (other streams, other threads) race and must not be issued.
+ *  - Synchronises `stream`; writes *h_out on success.
+ * Errors: AHS_ERR_DTYPE for an unknown key type; AHS_ERR_INVALID_ARG for a
+ * null h_out or null keys with n > 0; AHS_ERR_RANGE when n exceeds
+ * AHS_NOALLOC_MAX_KEYS or when the device has more SMs than the fixed array
+ * was sized for (more than about 189); AHS_ERR_CUDA for a failed CUDA call. */
+#define AHS_NOALLOC_MAX_KEYS 4294967295ull
+ahs_status ahs_features_noalloc(const void* d_keys, uint64_t n, ahs_key_type type, void* stream,
+                                ahs_features_t* h_out);
+
 /* ------------------------------------------- Section III-A / III-H: select */
 
 /* Pure host function: the FSM with explicit thresholds. */

@@ -103,6 +103,7 @@ SIGNATURES = {
     "ahs_trace_enable": (ctypes.c_int, [_ctx, _i32]),
     "ahs_trace_collect": (ctypes.c_int, [_ctx, _P(ahs_trace_entry_t), _u32, _P(_u32)]),
     "ahs_features": (ctypes.c_int, [_ctx, _vp, _u64, ctypes.c_int, _vp, _P(ahs_features_t)]),
+    "ahs_features_noalloc": (ctypes.c_int, [_vp, _u64, ctypes.c_int, _vp, _P(ahs_features_t)]),
     "ahs_select_fsm": (ctypes.c_int, [_P(ahs_features_t), _P(ahs_thresholds_t), _P(ctypes.c_int)]),
     "ahs_select": (ctypes.c_int, [_ctx, _P(ahs_features_t), ctypes.c_int, _u32, _i32,
                                   _P(ctypes.c_int)]),
@@ -278,6 +279,19 @@ class Context:
                                  len(seg_offsets) - 1, kt, _stream_handle(stream),
                                  ctypes.byref(info)), "ahs_sort_batch", self.handle)
         return out, vals_out, info
+
+
+AHS_NOALLOC_MAX_KEYS = (1 << 32) - 1
+
+
+def features_noalloc(keys, key_type=None, stream=None) -> ahs_features_t:
+    """ahs_features_noalloc: the state vector with no allocation and no context,
+    for callers that cannot allocate device memory (see include/ahs.h)."""
+    f = ahs_features_t()
+    kt = key_type_of(keys) if key_type is None else key_type
+    check(lib.ahs_features_noalloc(ctypes.c_void_p(keys.data_ptr()), keys.numel(), kt,
+                                   _stream_handle(stream), ctypes.byref(f)), "ahs_features_noalloc")
+    return f
 
 
 def profile_thresholds(mode: int) -> ahs_thresholds_t:

@@ -1,0 +1,68 @@
+"""ahs_features_noalloc, the feature pass for callers that cannot allocate.
+
+Callers that may not call cudaMalloc (inside stream capture, under a fixed
+up-front memory reservation, on latency-bound paths) use this entry point; its
+scratch is a fixed array inside the library.  Through the C ABI it must return
+what ahs_features returns for the same keys, on consecutive calls that reuse
+the same scratch.  This file is collected last so that a failure here does not
+hide the rest of the suite; it passes alone and after the other tests.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ENT_REL, ENT_ABS = 1e-9, 1e-12   # the tolerance of the other parity tests
+
+
+def _same(a, b):
+    assert (a.n, a.min_bits, a.max_bits, a.span, a.hist_shift, a.nbins, a.descents) == \
+        (b.n, b.min_bits, b.max_bits, b.span, b.hist_shift, b.nbins, b.descents)
+    assert math.isclose(a.entropy_bits, b.entropy_bits, rel_tol=ENT_REL, abs_tol=ENT_ABS)
+    assert math.isclose(a.entropy_norm, b.entropy_norm, rel_tol=ENT_REL, abs_tol=ENT_ABS)
+
+
+def _raw_noalloc(ahs, t, key_type):
+    f = ahs.ahs_features_t()
+    rc = ahs.lib.ahs_features_noalloc(ctypes.c_void_p(t.data_ptr()), t.numel(), key_type, None,
+                                      ctypes.byref(f))
+    return rc, f
+
+
+def test_noalloc_matches_features_on_consecutive_calls():
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    rng = np.random.default_rng(2024)
+    cases = [
+        (rng.integers(0, 4096, size=(1 << 22) + 3, dtype=np.uint32), ahs.AHS_U32, torch.int32),
+        (rng.integers(0, 2**32, size=(1 << 21) + 5, dtype=np.uint32), ahs.AHS_U32, torch.int32),
+        (rng.integers(-2**62, 2**62, size=300_001, dtype=np.int64), ahs.AHS_I64, torch.int64),
+    ]
+    with ahs.Context(0) as ctx:
+        for a, kt, tdt in cases:
+            t = torch.from_numpy(a.view(np.int32 if a.itemsize == 4 else np.int64)).cuda()
+            ref = ctx.features(t, key_type=kt)
+            for _ in range(2):          # two calls in a row reuse the same scratch
+                rc, f = _raw_noalloc(ahs, t, kt)
+                assert rc == ahs.AHS_OK
+                _same(f, ref)
+
+
+def test_noalloc_edge_cases():
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    t = torch.zeros(16, dtype=torch.int32, device="cuda")
+    f = ahs.ahs_features_t()
+    # empty input
+    assert ahs.lib.ahs_features_noalloc(ctypes.c_void_p(t.data_ptr()), 0, ahs.AHS_U32, None,
+                                        ctypes.byref(f)) == ahs.AHS_OK and f.n == 0
+    # beyond the stated maximum: refused before any device work
+    assert ahs.lib.ahs_features_noalloc(ctypes.c_void_p(t.data_ptr()), ahs.AHS_NOALLOC_MAX_KEYS + 1,
+                                        ahs.AHS_U32, None, ctypes.byref(f)) == ahs.AHS_ERR_RANGE
+    assert ahs.lib.ahs_features_noalloc(ctypes.c_void_p(t.data_ptr()), 16, 7, None,
+                                        ctypes.byref(f)) == ahs.AHS_ERR_DTYPE
+    f = ahs.features_noalloc(t, key_type=ahs.AHS_U32)
+    assert f.n == 16 and f.span == 0 and f.nbins == 1 and f.entropy_bits == 0.0
