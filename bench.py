@@ -347,6 +347,57 @@ def run_ours(args, world, rank, local):
     ctx.close()
 
 
+def run_case(args, local):
+    """One workload array with one (possibly forced) strategy: per-kernel
+    device times from the library trace.  Used for per-strategy rooflines and
+    as the small case under ncu."""
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2506_20677_gb300 as ahs
+    from gen import device as gdev
+    force = {"auto": ahs.AHS_AUTO, "counting": ahs.AHS_COUNTING, "radix": ahs.AHS_RADIX,
+             "general": ahs.AHS_GENERAL}[args.force]
+    if args.case == "3":
+        keys, vals = gdev.config3(args.n)
+        kt, w, v = ahs.AHS_U64, 8, 4
+    else:
+        keys, vals = gdev.config2(args.case, args.n), None
+        kt, w, v = ahs.AHS_U32, 4, 0
+    out = torch.empty_like(keys)
+    vout = torch.empty_like(vals) if vals is not None else None
+    ctx = ahs.Context(local)
+    for _ in range(args.warmup):
+        ctx.sort(keys, vals=vals, out=out, vals_out=vout, force=force, key_type=kt)
+    torch.cuda.synchronize()
+    ctx.trace(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        r = ctx.sort(keys, vals=vals, out=out, vals_out=vout, force=force, key_type=kt)
+    e1.record()
+    torch.cuda.synchronize()
+    trace = ctx.trace_collect()
+    ms = e0.elapsed_time(e1) / args.steps
+    peak, kind = measured_peaks()
+    import collections
+    kt_ = collections.defaultdict(lambda: [0, 0.0, 0])
+    for name, items, t in trace:
+        kt_[name][0] += 1
+        kt_[name][1] += t
+        kt_[name][2] += items
+    kernels = {}
+    for name, (c, t, items) in sorted(kt_.items(), key=lambda kv: -kv[1][1]):
+        b = algo_bytes_per_item(name, w, v) * items / c
+        kernels[name] = {"launches": c, "avg_ms": round(t / c, 4),
+                         "gbs": round(b / (t / c / 1e3) / 1e9, 1) if b else None,
+                         "frac": round(b / (t / c / 1e3) / 1e9 / peak, 4) if b else None}
+    print(json.dumps({"case": args.case, "force": args.force, "n": args.n,
+                      "strategy": ahs.STRATEGY_NAMES[r.strategy], "ms_per_sort": round(ms, 4),
+                      "gkeys_s": round(args.n / (ms / 1e3) / 1e9, 3), "peak_gbs": peak,
+                      "peak_kind": kind, "kernels": kernels}), flush=True)
+    ctx.close()
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -357,8 +408,14 @@ def main():
     p.add_argument("--ref-sample", type=int, default=1 << 22,
                    help="keys per array the CPU oracle sorts")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--case", choices=list(VARIANTS) + ["3"], default=None,
+                   help="diagnostic: one array of config 2 (a-f) or config 3, see --force")
+    p.add_argument("--force", choices=["auto", "counting", "radix", "general"], default="auto")
     args = p.parse_args()
     world, rank, local = dist_setup()
+    if args.case is not None:
+        run_case(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -17,11 +17,8 @@ namespace ahs {
 namespace {
 
 constexpr int kK1Threads = 512;
-constexpr int kK1Unroll = 4;
+constexpr int kK1Unroll = 8;
 constexpr int kK2Unroll = 4;
-constexpr uint32_t kCounterBits = 21;                       // packed shared-memory counters
-constexpr unsigned long long kCounterMask = (1ull << kCounterBits) - 1;
-constexpr uint32_t kPackedWords = kHistSmemBytes / 8;       // 21,846 words, 3 counters each
 constexpr uint32_t kU32Bins = kHistSmemBytes / 4;           // bins that fit as u32 counters
 
 template <typename K>
@@ -34,7 +31,7 @@ __device__ __forceinline__ void k1_scalar(const K* keys, uint64_t i, uint64_t n,
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kK1Threads)
+__global__ void __launch_bounds__(kK1Threads, 2)
 k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
                    unsigned long long* __restrict__ partials, DevFeatures* __restrict__ rec) {
     constexpr int V = Vec16<K>::kN;
@@ -146,55 +143,44 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
     }
 }
 
-// Per-CTA shared histogram.  PACKED: 65,536 bins as 21-bit counters, three per
-// 64-bit word (174,768 bytes); a CTA flushes before any counter can reach 2^21.
-// Otherwise: u32 counters, replicated R times (warp w uses copy w % R) to
-// spread same-bin atomics of skewed inputs.
-template <typename K, bool PACKED>
-__device__ __forceinline__ void k2_body(const K* __restrict__ keys, uint64_t n, K flip,
-                                        uint64_t head, uint64_t nvec, K mn, uint32_t s,
-                                        uint32_t nb, uint32_t R, uint32_t* __restrict__ slabs,
-                                        unsigned long long* sm64) {
+// K2: per-CTA shared-memory histograms of u32 counters, flushed to per-slab
+// counts in global memory.  Two layouts, chosen on the device from nbins:
+//  - nbins <= kU32Bins (43,692): every CTA counts all bins of the keys it
+//    reads, in R copies (warp w uses copy w % R) that spread the same-bin
+//    atomics of skewed inputs; one slab per CTA.
+//  - larger (up to 65,536 bins): the two CTAs of a cluster read the same
+//    chunks and each counts only its half of the bins (32,768 u32 counters,
+//    128 KB), so no counter needs more than 32 bits and no atomic is wider
+//    than 32 bits; the second read of a chunk is served by L2.  One slab per
+//    cluster.
+template <typename K>
+__device__ __forceinline__ void k2_load(const K* __restrict__ body, uint64_t c, uint64_t nvec,
+                                        Vec16<K> (&x)[kK2Unroll], bool (&ok)[kK2Unroll]) {
+    constexpr uint64_t kChunkVecs = (uint64_t)kHistThreads * kK2Unroll;
+#pragma unroll
+    for (int u = 0; u < kK2Unroll; ++u) {
+        const uint64_t v = c * kChunkVecs + (uint64_t)u * kHistThreads + threadIdx.x;
+        ok[u] = v < nvec;
+        if (ok[u]) x[u] = load_vec16(body + v * Vec16<K>::kN);
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ void k2_replicated(const K* __restrict__ keys, uint64_t n, K flip,
+                                              uint64_t head, uint64_t nvec, K mn, uint32_t s,
+                                              uint32_t nb, uint32_t* __restrict__ slabs,
+                                              uint32_t* sm) {
     constexpr int V = Vec16<K>::kN;
     constexpr uint64_t kChunkVecs = (uint64_t)kHistThreads * kK2Unroll;
-    // Chunks per epoch: keep every packed counter below 2^21 (with margin for
-    // the <= 2V scalar head/tail keys counted by CTA 0).
-    constexpr uint32_t kEpochChunks = (uint32_t)(((1u << kCounterBits) - 1 - 2 * V) / (kChunkVecs * V));
-    uint32_t* sm32 = reinterpret_cast<uint32_t*>(sm64);
-    const uint32_t warp = threadIdx.x >> 5;
-    uint32_t* mine = sm32 + (warp % R) * nb;
-
+    uint32_t R = kU32Bins / nb;
+    R = R > 32 ? 32 : R;
+    for (uint32_t i = threadIdx.x; i < R * nb; i += kHistThreads) sm[i] = 0;
+    __syncthreads();
+    uint32_t* mine = sm + ((threadIdx.x >> 5) % R) * nb;
     auto add = [&](K x) {
         const uint32_t bin = (uint32_t)(((K)(x ^ flip) - mn) >> s);
-        if (!AHS_DCHECK(bin < nb, "k2 bin", bin)) return;
-        if constexpr (PACKED) atomicAdd(&sm64[bin / 3], 1ull << (kCounterBits * (bin % 3)));
-        else atomicAdd(&mine[bin], 1u);
+        if (AHS_DCHECK(bin < nb, "k2 bin", bin)) atomicAdd(&mine[bin], 1u);
     };
-    auto clear = [&]() {
-        if constexpr (PACKED) {
-            for (uint32_t i = threadIdx.x; i < kPackedWords; i += kHistThreads) sm64[i] = 0;
-        } else {
-            for (uint32_t i = threadIdx.x; i < R * nb; i += kHistThreads) sm32[i] = 0;
-        }
-    };
-    uint32_t* slab = slabs + (size_t)blockIdx.x * kMaxBins;
-    auto flush = [&](bool first) {
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < nb; j += kHistThreads) {
-            uint32_t c;
-            if constexpr (PACKED) {
-                c = (uint32_t)((sm64[j / 3] >> (kCounterBits * (j % 3))) & kCounterMask);
-            } else {
-                c = 0;
-                for (uint32_t r = 0; r < R; ++r) c += sm32[r * nb + j];
-            }
-            slab[j] = first ? c : slab[j] + c;
-        }
-        __syncthreads();
-    };
-
-    clear();
-    __syncthreads();
     if (blockIdx.x == 0) {
         const uint64_t tail0 = head + nvec * V;
         if (threadIdx.x < head) add(keys[threadIdx.x]);
@@ -202,56 +188,83 @@ __device__ __forceinline__ void k2_body(const K* __restrict__ keys, uint64_t n, 
     }
     const K* body = keys + head;
     const uint64_t nchunks = ceil_div(nvec, kChunkVecs);
-    bool first = true;
-    uint32_t in_epoch = 0;
     for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         Vec16<K> x[kK2Unroll];
         bool ok[kK2Unroll];
-#pragma unroll
-        for (int u = 0; u < kK2Unroll; ++u) {
-            const uint64_t v = c * kChunkVecs + (uint64_t)u * kHistThreads + threadIdx.x;
-            ok[u] = v < nvec;
-            if (ok[u]) x[u] = load_vec16_stream(body + v * V);
-        }
+        k2_load(body, c, nvec, x, ok);
 #pragma unroll
         for (int u = 0; u < kK2Unroll; ++u)
             if (ok[u]) {
 #pragma unroll
                 for (int j = 0; j < V; ++j) add(x[u].e[j]);
             }
-        if (PACKED && ++in_epoch == kEpochChunks) {
-            flush(first);
-            first = false;
-            in_epoch = 0;
-            clear();
-            __syncthreads();
-        }
     }
-    flush(first);
+    __syncthreads();
+    uint32_t* slab = slabs + (size_t)blockIdx.x * kMaxBins;
+    for (uint32_t j = threadIdx.x; j < nb; j += kHistThreads) {
+        uint32_t c = 0;
+        for (uint32_t r = 0; r < R; ++r) c += sm[r * nb + j];
+        slab[j] = c;
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ void k2_split(const K* __restrict__ keys, uint64_t n, K flip,
+                                         uint64_t head, uint64_t nvec, K mn, uint32_t s,
+                                         uint32_t nb, uint32_t* __restrict__ slabs, uint32_t* sm) {
+    constexpr int V = Vec16<K>::kN;
+    constexpr uint64_t kChunkVecs = (uint64_t)kHistThreads * kK2Unroll;
+    const uint32_t h = blockIdx.x & 1u, pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const uint32_t half = (nb + 1) >> 1;
+    const uint32_t lo = h * half;
+    const uint32_t len = h ? nb - half : half;
+    for (uint32_t i = threadIdx.x; i < len; i += kHistThreads) sm[i] = 0;
+    __syncthreads();
+    auto add = [&](K x) {
+        const uint32_t b = (uint32_t)(((K)(x ^ flip) - mn) >> s) - lo;   // wraps below lo
+        if (b < len) atomicAdd(&sm[b], 1u);
+    };
+    if (pair == 0) {
+        const uint64_t tail0 = head + nvec * V;
+        if (threadIdx.x < head) add(keys[threadIdx.x]);
+        if (threadIdx.x < n - tail0) add(keys[tail0 + threadIdx.x]);
+    }
+    const K* body = keys + head;
+    const uint64_t nchunks = ceil_div(nvec, kChunkVecs);
+    for (uint64_t c = pair; c < nchunks; c += npairs) {
+        Vec16<K> x[kK2Unroll];
+        bool ok[kK2Unroll];
+        k2_load(body, c, nvec, x, ok);
+#pragma unroll
+        for (int u = 0; u < kK2Unroll; ++u)
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) add(x[u].e[j]);
+            }
+    }
+    __syncthreads();
+    uint32_t* slab = slabs + (size_t)pair * kMaxBins + lo;
+    for (uint32_t j = threadIdx.x; j < len; j += kHistThreads) slab[j] = sm[j];
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kHistThreads, 1)
 k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
              const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs) {
-    extern __shared__ __align__(16) unsigned long long sm64[];
+    extern __shared__ __align__(16) uint32_t sm32[];
     const K mn = (K)rec->min_ord;
     const uint32_t s = rec->shift;
     const uint32_t nb = rec->nbins;
-    if (nb > kU32Bins) {
-        k2_body<K, true>(keys, n, flip, head, nvec, mn, s, nb, 1, slabs, sm64);
-    } else {
-        uint32_t R = kU32Bins / nb;
-        R = R > 32 ? 32 : R;
-        k2_body<K, false>(keys, n, flip, head, nvec, mn, s, nb, R, slabs, sm64);
-    }
+    if (nb > kU32Bins) k2_split<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
+    else k2_replicated<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
 }
 
 __global__ void __launch_bounds__(256)
-k3_entropy(const uint32_t* __restrict__ slabs, uint32_t nslabs, uint64_t n,
+k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
            DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
            double* __restrict__ partials) {
     const uint32_t nb = rec->nbins;
+    const uint32_t nslabs = nb > kU32Bins ? k2_grid / 2 : k2_grid;   // see K2's two layouts
     const uint32_t j = blockIdx.x * 256 + threadIdx.x;
     double term = 0.0;
     if (j < nb) {
@@ -305,11 +318,26 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
         k1_minmax_descents<K><<<g1, kK1Threads, 0, st>>>(keys, n, flip, head, nvec, s.k1_partials,
                                                           s.rec);
     }
-    const uint32_t g2 = (uint32_t)sms;
+    // One CTA per SM (shared memory holds one histogram), launched as clusters
+    // of two so that a pair shares a GPC and its duplicated reads hit L2.
+    const uint32_t g2 = (uint32_t)(sms & ~1);
     {
         TraceScope ts("features_histogram", n, st);
-        k2_histogram<K><<<g2, kHistThreads, kHistSmemBytes, st>>>(keys, n, flip, head, nvec, s.rec,
-                                                                  s.slabs);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g2);
+        cfg.blockDim = dim3(kHistThreads);
+        cfg.dynamicSmemBytes = kHistSmemBytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k2_histogram<K>, keys, n, flip, head, nvec,
+                                           (const DevFeatures*)s.rec, s.slabs);
+        if (e != cudaSuccess) return e;
     }
     {
         TraceScope ts("features_entropy", 0, st);
@@ -323,7 +351,7 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
 uint32_t k1_blocks(uint64_t n, int sms) {
     const uint64_t per = (uint64_t)kK1Threads * kK1Unroll * 4;
     uint64_t b = ceil_div(n ? n : 1, per);
-    const uint64_t cap = 4ull * (uint64_t)sms;
+    const uint64_t cap = 2ull * (uint64_t)sms;   // two resident blocks per SM: one wave
     return (uint32_t)(b < cap ? b : cap);
 }
 

@@ -29,7 +29,7 @@ struct DevFeatures {
 static_assert(sizeof(DevFeatures) == 128, "DevFeatures layout");
 
 constexpr uint32_t kMaxBins = 1u << 16;             // histogram bins, Section III-A reading
-constexpr uint32_t kHistSmemBytes = 21846u * 8u;    // 65,536 21-bit counters, 3 per u64 word
+constexpr uint32_t kHistSmemBytes = 21846u * 8u;    // shared memory of the histogram kernel
 constexpr uint32_t kHistThreads = 1024;
 constexpr uint32_t kEntropyBlocks = kMaxBins / 256;
 
