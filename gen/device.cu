@@ -85,6 +85,71 @@ __global__ void k_swaps_u32(uint32_t* a, unsigned long long n, unsigned long lon
     }
 }
 
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Batch of segments (one CTA each): type 0 uniform below 4096, 1 Zipf over
+// 1,024 distinct values of the segment, 2 and 3 uniform 32-bit (type 3 is
+// sorted and swapped afterwards).  Streams per segment s: keys 16 + 4 s,
+// Zipf values 16 + 4 s + 1 (as gen/host.py segment_stream).
+__global__ void k_batch_u32(uint32_t* out, const unsigned long long* offs, const unsigned char* types,
+                            unsigned long long seed, const double* cdf, uint32_t nv) {
+    const unsigned s = blockIdx.x;
+    const unsigned long long b = offs[s], n = offs[s + 1] - offs[s];
+    const unsigned long long key = stream_key(seed, 16ull + 4ull * s);
+    const unsigned t = types[s];
+    uint32_t k1 = 0, k2 = 0;
+    if (t == 1) {
+        const unsigned long long kz = mix64(stream_key(seed, 16ull + 4ull * s + 1) + kGolden);
+        k1 = (uint32_t)kz;
+        k2 = (uint32_t)(kz >> 32);
+    }
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long r = draw(key, i);
+        uint32_t v;
+        if (t == 0) {
+            v = (uint32_t)(((r >> 32) * 4096ull) >> 32);
+        } else if (t == 1) {
+            const double u = (double)(r >> 11) * 0x1.0p-53;
+            uint32_t lo = 0, hi = nv;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (cdf[mid] > u) hi = mid;
+                else lo = mid + 1;
+            }
+            const uint32_t rank = lo < nv ? lo : nv - 1;
+            v = hash32(rank ^ k1) ^ k2;
+        } else {
+            v = (uint32_t)(r >> 32);
+        }
+        out[b + i] = v;
+    }
+}
+
+// Per listed segment, its floor(n / 100) sequential swaps (one thread each).
+__global__ void k_batch_swaps(uint32_t* out, const unsigned long long* offs, const unsigned* segs,
+                              unsigned nlist, unsigned long long seed) {
+    const unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nlist) return;
+    const unsigned s = segs[j];
+    const unsigned long long b = offs[s], n = offs[s + 1] - offs[s];
+    const unsigned long long key = stream_key(seed, 16ull + 4ull * s + 2);
+    uint32_t* a = out + b;
+    for (unsigned long long t = 0; t < n / 100; ++t) {
+        const unsigned long long i = __umul64hi(draw(key, 2 * t), n);
+        const unsigned long long k = __umul64hi(draw(key, 2 * t + 1), n);
+        const uint32_t x = a[i];
+        a[i] = a[k];
+        a[k] = x;
+    }
+}
+
 unsigned grid(unsigned long long n) {
     unsigned long long g = (n + 255) / 256;
     return (unsigned)(g < 8192 ? (g ? g : 1) : 8192);
@@ -135,6 +200,23 @@ int gen_swaps_u32(void* a, unsigned long long n, unsigned long long swaps, unsig
                   unsigned long long stream, void* st) {
     if (n == 0 || swaps == 0) return 0;
     k_swaps_u32<<<1, 1, 0, (cudaStream_t)st>>>((uint32_t*)a, n, swaps, stream_key(seed, stream));
+    return (int)cudaGetLastError();
+}
+
+int gen_batch_u32(void* out, const void* d_offs, const void* d_types, unsigned nseg,
+                  unsigned long long seed, const void* d_cdf, unsigned nv, void* st) {
+    if (nseg == 0) return 0;
+    k_batch_u32<<<nseg, 256, 0, (cudaStream_t)st>>>((uint32_t*)out, (const unsigned long long*)d_offs,
+                                                    (const unsigned char*)d_types, seed,
+                                                    (const double*)d_cdf, nv);
+    return (int)cudaGetLastError();
+}
+
+int gen_batch_swaps(void* out, const void* d_offs, const void* d_segs, unsigned nlist,
+                    unsigned long long seed, void* st) {
+    if (nlist == 0) return 0;
+    k_batch_swaps<<<(nlist + 127) / 128, 128, 0, (cudaStream_t)st>>>(
+        (uint32_t*)out, (const unsigned long long*)d_offs, (const unsigned*)d_segs, nlist, seed);
     return (int)cudaGetLastError();
 }
 

@@ -28,6 +28,8 @@ def lib():
         L.gen_ramp_steps.argtypes = [vp, u64, u64, u64, vp]
         L.gen_ramp_replace.argtypes = [vp, u64, u64, u64, u64, u64, vp]
         L.gen_swaps_u32.argtypes = [vp, u64, u64, u64, u64, vp]
+        L.gen_batch_u32.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp, ctypes.c_uint, vp]
+        L.gen_batch_swaps.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp]
         _lib = L
     return _lib
 
@@ -105,3 +107,45 @@ def config3(n=H.N_CFG3, seed=H.SEED_CFG3, t0=1_700_000_000_000_000_000, max_step
     _ok(lib().gen_ramp_replace(t.data_ptr(), n, seed, H.REPLACE_53, t0, rng % (1 << 64), _st()))
     vals = torch.arange(n, dtype=torch.int32, device="cuda")
     return t, vals
+
+
+def config4(n_seg=100_000, seed=H.SEED_CFG4, lo=16, hi=1 << 20, sort_chunk_keys=1 << 27):
+    """Batch of uneven segments: (keys int32 tensor, offsets np.uint64, lengths, types).
+
+    Types index gen.host.SEG_TYPES = (a, b, c, e); each segment is generated
+    from (seed, segment id) exactly as gen.host.config4_segment.  Type (e)
+    segments are sorted (PyTorch, by (segment, key)) and then swapped."""
+    import torch
+    lengths, types, offsets = H.config4_layout(n_seg, seed, lo, hi)
+    total = int(offsets[-1])
+    out = torch.empty(total, dtype=torch.int32, device="cuda")
+    d_offs = torch.from_numpy(offsets.view(np.int64)).cuda()
+    d_types = torch.from_numpy(types.astype(np.uint8)).cuda()
+    cdf = torch.from_numpy(H.zipf_cdf(1024, 1.1)).cuda()
+    _ok(lib().gen_batch_u32(out.data_ptr(), d_offs.data_ptr(), d_types.data_ptr(), n_seg, seed,
+                            cdf.data_ptr(), 1024, _st()))
+    # sort every type-(e) segment: groups of consecutive e-segments by key size
+    e_segs = np.nonzero(types == 3)[0]
+    i = 0
+    while i < len(e_segs):
+        j, keys = i, 0
+        while j < len(e_segs) and (j == i or keys + int(lengths[e_segs[j]]) <= sort_chunk_keys):
+            keys += int(lengths[e_segs[j]])
+            j += 1
+        parts = [out[int(offsets[s]):int(offsets[s + 1])] for s in e_segs[i:j]]
+        cat = torch.cat(parts).to(torch.int64) & 0xFFFFFFFF
+        tag = torch.repeat_interleave(torch.arange(j - i, device="cuda", dtype=torch.int64),
+                                      torch.tensor([int(lengths[s]) for s in e_segs[i:j]],
+                                                   device="cuda"))
+        srt = torch.sort((tag << 32) | cat).values & 0xFFFFFFFF
+        at = 0
+        for s in e_segs[i:j]:
+            L = int(lengths[s])
+            out[int(offsets[s]):int(offsets[s + 1])] = srt[at:at + L].to(torch.int32)
+            at += L
+        i = j
+    d_e = torch.from_numpy(e_segs.astype(np.uint32).view(np.int32)).cuda()
+    _ok(lib().gen_batch_swaps(out.data_ptr(), d_offs.data_ptr(), d_e.data_ptr(), len(e_segs), seed,
+                              _st()))
+    torch.cuda.synchronize()
+    return out, offsets, lengths, types

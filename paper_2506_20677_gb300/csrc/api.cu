@@ -96,15 +96,23 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
 
 ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload) {
     ahs_thresholds_t t;
+    ahs_strategy s;
     switch (ctx->cfg.select_mode) {
     case AHS_SEL_MODEL:
-        return select_model(ctx->model, f, key_bytes, payload ? 1 : 0);
+        s = select_model(ctx->model, f, key_bytes, payload ? 1 : 0);
+        break;
     case AHS_SEL_CUSTOM:
-        return select_fsm(f, ctx->custom);
+        s = select_fsm(f, ctx->custom);
+        break;
     default:
         profile_thresholds(ctx->cfg.select_mode, &t);
-        return select_fsm(f, t);
+        s = select_fsm(f, t);
+        break;
     }
+    // Insertion-sort sized inputs run in one CTA; a profile whose n_t exceeds
+    // that capacity sends the rest to the general path.
+    if (s == AHS_SMALL && f.n > blocksort_capacity(key_bytes, payload)) s = AHS_GENERAL;
+    return s;
 }
 
 ahs_status ensure_aux(ahs_ctx* ctx, size_t bytes) {

@@ -17,17 +17,20 @@ blocksort_single(const K* keys_in, K* keys_out, const uint32_t* vals_in, uint32_
     block_sort<K, VALS, T, IPT>(keys_in, keys_out, vals_in, vals_out, n, flip, S);
 }
 
-// One CTA per final bucket: sort src[begin, begin+size) into dst (sorted
-// buckets), or copy it (buckets whose keys are all equal need no pass).
+// One CTA per final bucket: sort src[begin, begin+size) into out (sorted
+// buckets), or copy it (buckets whose keys are all equal need no pass).  The
+// source is buffer 0 (temporary), 1 (the output itself) or 2 (the input).
 template <typename K, bool VALS, int T, int IPT>
 __global__ void __launch_bounds__(T)
-bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1, K* out,
-              const uint32_t* vbuf0, const uint32_t* vbuf1, uint32_t* vout, K flip) {
+bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1, const K* buf2,
+              K* out, const uint32_t* vbuf0, const uint32_t* vbuf1, const uint32_t* vbuf2,
+              uint32_t* vout, K flip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<BlockSortSmem<K, VALS, T, IPT>*>(smem_raw);
     const FinalBucket b = list[blockIdx.x];
-    const K* src = (b.where == 0 ? buf0 : buf1) + b.begin;
-    const uint32_t* vsrc = VALS ? (b.where == 0 ? vbuf0 : vbuf1) + b.begin : nullptr;
+    const K* src = (b.where == 0 ? buf0 : (b.where == 1 ? buf1 : buf2)) + b.begin;
+    const uint32_t* vsrc =
+        VALS ? (b.where == 0 ? vbuf0 : (b.where == 1 ? vbuf1 : vbuf2)) + b.begin : nullptr;
     K* dst = out + b.begin;
     uint32_t* vdst = VALS ? vout + b.begin : nullptr;
     if (b.sort) {
@@ -56,8 +59,9 @@ cudaError_t single_t(const void* kin, void* kout, const uint32_t* vin, uint32_t*
 
 template <typename K, bool VALS, int T, int IPT>
 cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t keys, const void* b0,
-                         const void* b1, void* out, const uint32_t* vb0, const uint32_t* vb1,
-                         uint32_t* vout, K flip, cudaStream_t st) {
+                         const void* b1, const void* b2, void* out, const uint32_t* vb0,
+                         const uint32_t* vb1, const uint32_t* vb2, uint32_t* vout, K flip,
+                         cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     using Smem = BlockSortSmem<K, VALS, T, IPT>;
     auto fn = bucket_finish<K, VALS, T, IPT>;
@@ -67,23 +71,24 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
     // Grids are limited to 2^31 - 1 blocks in x; bucket lists are far smaller.
     TraceScope ts(T == 128 ? "bucket_sort_1k" : (T == 256 ? "bucket_sort_4k" : "bucket_sort_8k"), keys, st);
     fn<<<count, T, sizeof(Smem), st>>>(d_list, static_cast<const K*>(b0), static_cast<const K*>(b1),
-                                       static_cast<K*>(out), vb0, vb1, vout, flip);
+                                       static_cast<const K*>(b2), static_cast<K*>(out), vb0, vb1,
+                                       vb2, vout, flip);
     return cudaGetLastError();
 }
 
 template <typename K, bool VALS>
 cudaError_t finish_t(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                     const uint64_t keys[3], const void* b0, const void* b1, void* out,
-                     const uint32_t* vb0, const uint32_t* vb1, uint32_t* vout, K flip,
-                     cudaStream_t st) {
-    cudaError_t e = finish_class<K, VALS, 128, 8>(d_lists[0], counts[0], keys[0], b0, b1, out, vb0,
-                                                  vb1, vout, flip, st);
+                     const uint64_t keys[3], const void* b0, const void* b1, const void* b2,
+                     void* out, const uint32_t* vb0, const uint32_t* vb1, const uint32_t* vb2,
+                     uint32_t* vout, K flip, cudaStream_t st) {
+    cudaError_t e = finish_class<K, VALS, 128, 8>(d_lists[0], counts[0], keys[0], b0, b1, b2, out,
+                                                  vb0, vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 256, 16>(d_lists[1], counts[1], keys[1], b0, b1, out, vb0, vb1,
-                                           vout, flip, st);
+        e = finish_class<K, VALS, 256, 16>(d_lists[1], counts[1], keys[1], b0, b1, b2, out, vb0,
+                                           vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 512, 16>(d_lists[2], counts[2], keys[2], b0, b1, out, vb0, vb1,
-                                           vout, flip, st);
+        e = finish_class<K, VALS, 512, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
+                                           vb1, vb2, vout, flip, st);
     return e;
 }
 
@@ -116,19 +121,20 @@ cudaError_t launch_blocksort_single(const void* keys_in, void* keys_out, const u
 }
 
 cudaError_t launch_bucket_finish(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                                 const uint64_t keys[3], const void* buf0, const void* buf1, void* out,
-                                 const uint32_t* vbuf0, const uint32_t* vbuf1, uint32_t* vout,
+                                 const uint64_t keys[3], const void* buf0, const void* buf1,
+                                 const void* buf2, void* out, const uint32_t* vbuf0,
+                                 const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
                                  KeyDesc kd, cudaStream_t st) {
-    const bool v = vout != nullptr;
+    const bool v = vout != nullptr && vbuf2 != nullptr;
     if (kd.bytes == 4)
-        return v ? finish_t<uint32_t, true>(d_lists, counts, keys, buf0, buf1, out, vbuf0, vbuf1, vout,
-                                           (uint32_t)kd.flip, st)
-                 : finish_t<uint32_t, false>(d_lists, counts, keys, buf0, buf1, out, nullptr, nullptr,
-                                            nullptr, (uint32_t)kd.flip, st);
-    return v ? finish_t<uint64_t, true>(d_lists, counts, keys, buf0, buf1, out, vbuf0, vbuf1, vout,
-                                       kd.flip, st)
-             : finish_t<uint64_t, false>(d_lists, counts, keys, buf0, buf1, out, nullptr, nullptr,
-                                        nullptr, kd.flip, st);
+        return v ? finish_t<uint32_t, true>(d_lists, counts, keys, buf0, buf1, buf2, out, vbuf0,
+                                           vbuf1, vbuf2, vout, (uint32_t)kd.flip, st)
+                 : finish_t<uint32_t, false>(d_lists, counts, keys, buf0, buf1, buf2, out, nullptr,
+                                            nullptr, nullptr, nullptr, (uint32_t)kd.flip, st);
+    return v ? finish_t<uint64_t, true>(d_lists, counts, keys, buf0, buf1, buf2, out, vbuf0, vbuf1,
+                                       vbuf2, vout, kd.flip, st)
+             : finish_t<uint64_t, false>(d_lists, counts, keys, buf0, buf1, buf2, out, nullptr,
+                                        nullptr, nullptr, nullptr, kd.flip, st);
 }
 
 }  // namespace ahs

@@ -11,6 +11,11 @@
 //   sample -> count (per tile, per bucket) -> segmented column scan -> stable scatter
 // and a bucket that fits one CTA (<= 8,192 keys) is sorted in shared memory.
 // Every step is stable, so a payload comes out in the unique stable order.
+//
+// The same partition kernels, with the bucket of a key taken as an 8-bit digit
+// of (key - segment min) instead of its splitter interval, give a segmented
+// LSD radix sort for the batched form (many arrays sorted in one launch per
+// pass).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -20,6 +25,7 @@
 #include "ctx.h"
 #include "internal.h"
 #include "samplesort.h"
+#include "segsort.h"
 #include "trace.h"
 
 namespace ahs {
@@ -29,18 +35,23 @@ constexpr int kThreads = 512;
 constexpr int kIpt = 16;
 constexpr uint32_t kTile = kThreads * kIpt;     // keys per partition tile
 constexpr uint32_t kMaxSplit = 255;             // distinct splitters per segment
+constexpr uint32_t kSlots = 256;                // per segment: tree[1..255] then sorted[0..255]
 constexpr uint32_t kCols = 512;                 // 2 * 255 + 1 buckets, padded
 constexpr uint32_t kOversample = 32;
 constexpr uint32_t kSamples = (kMaxSplit + 1) * kOversample;   // 8,192
 constexpr uint32_t kChunkTiles = 32;
 constexpr uint32_t kMaxLevels = 16;
+constexpr int kSplit = 0;                       // bucket = splitter interval / equality
+constexpr int kDigit = 1;                       // bucket = 8-bit digit of key - segment min
+constexpr int kHistCopies = 4;
 
 struct SegDesc {
     unsigned long long begin;
     uint32_t size;
     uint32_t first_chunk;
     uint32_t nchunks;
-    uint32_t pad[3];
+    uint32_t pad;
+    unsigned long long min_ord;
 };
 struct TileDesc {
     unsigned long long begin;
@@ -62,25 +73,35 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-// Bucket of ord value o among m distinct ascending splitters sp:
-// 2j for sp[j-1] < o < sp[j], 2j+1 for o == sp[j].
+// Splitter bucket of ord value o: descend the implicit binary tree of the 255
+// (padded) splitters without branches -- after 8 levels j - 256 is the number
+// of splitters below o -- then test equality with that splitter.
+// 2j for sorted[j-1] < o < sorted[j], 2j+1 for o == sorted[j].
 template <typename K>
-__device__ __forceinline__ uint32_t classify(const K* sp, uint32_t m, K o) {
-    uint32_t lo = 0, len = m;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (sp[lo + half] < o) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return (lo < m && sp[lo] == o) ? 2 * lo + 1 : 2 * lo;
+__device__ __forceinline__ uint32_t classify_split(const K* tree, const K* sorted, uint32_t m, K o) {
+    uint32_t j = 1;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) j = 2 * j + (o > tree[j] ? 1u : 0u);
+    const uint32_t idx = j - 256;
+    return (idx < m && sorted[idx] == o) ? 2 * idx + 1 : 2 * idx;
 }
 
+template <typename K, int MODE>
+struct Classifier {
+    const K* tree;
+    const K* sorted;
+    uint32_t m;
+    K mn;
+    uint32_t shift;
+    __device__ __forceinline__ uint32_t operator()(K o) const {
+        if constexpr (MODE == kSplit) return classify_split(tree, sorted, m, o);
+        else return (uint32_t)((K)(o - mn) >> shift) & 0xffu;
+    }
+};
+
 // One CTA per segment: draw kSamples keys at hashed positions, sort them in
-// shared memory, keep the distinct values among the 255 quantiles.
+// shared memory, keep the distinct values among the 255 quantiles, pad with
+// the largest value and lay them out as an implicit search tree.
 template <typename K>
 __global__ void __launch_bounds__(kThreads)
 ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t level, K flip,
@@ -88,6 +109,7 @@ ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Smem = BlockSortSmem<K, false, kThreads, kIpt>;
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    __shared__ K s_sorted[kSlots];
     const SegDesc sg = segs[blockIdx.x];
     const unsigned long long salt =
         ((unsigned long long)level << 48) ^ ((unsigned long long)blockIdx.x << 20);
@@ -107,31 +129,57 @@ ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t 
     }
     uint32_t total;
     const uint32_t at = block_exclusive_scan<kThreads>(keep, S.scan, &total);
-    if (keep) splitters[(size_t)blockIdx.x * (kMaxSplit + 1) + at] = cand;
+    if (keep) s_sorted[at] = cand;
+    __syncthreads();
+    for (uint32_t i = total + threadIdx.x; i < kSlots; i += kThreads) s_sorted[i] = ~K(0);
+    __syncthreads();
+    K* out = splitters + (size_t)blockIdx.x * 2 * kSlots;
+    if (threadIdx.x < kSlots) {
+        const uint32_t j = threadIdx.x;
+        out[kSlots + j] = s_sorted[j];
+        if (j >= 1) {
+            const uint32_t d = 31 - __clz(j);              // depth of node j
+            const uint32_t p = j - (1u << d);              // position within its level
+            out[j] = s_sorted[((2 * p + 1) << (7 - d)) - 1];
+        } else {
+            out[0] = 0;
+        }
+    }
     if (threadIdx.x == 0) nsplit[blockIdx.x] = total;
 }
 
-// Per tile: bucket histogram.
-template <typename K>
+// Per tile: bucket histogram (4 copies spread the atomics of skewed inputs).
+template <typename K, int MODE>
 __global__ void __launch_bounds__(kThreads)
-ss_count(const K* __restrict__ src, const TileDesc* __restrict__ tiles, const K* __restrict__ splitters,
-         const uint32_t* __restrict__ nsplit, K flip, uint32_t* __restrict__ counts) {
-    __shared__ K sp[kMaxSplit + 1];
-    __shared__ uint32_t hist[kCols];
+ss_count(const K* __restrict__ src, const TileDesc* __restrict__ tiles,
+         const SegDesc* __restrict__ segs, const K* __restrict__ splitters,
+         const uint32_t* __restrict__ nsplit, K flip, uint32_t shift, uint32_t* __restrict__ counts) {
+    __shared__ K s_sp[2 * kSlots];
+    __shared__ uint32_t hist[kHistCopies][kCols];
     const TileDesc t = tiles[blockIdx.x];
-    const uint32_t m = nsplit[t.seg];
-    for (uint32_t i = threadIdx.x; i < m; i += kThreads) sp[i] = splitters[(size_t)t.seg * (kMaxSplit + 1) + i];
-    for (uint32_t i = threadIdx.x; i < kCols; i += kThreads) hist[i] = 0;
+    Classifier<K, MODE> cls{};
+    if constexpr (MODE == kSplit) {
+        const K* g = splitters + (size_t)t.seg * 2 * kSlots;
+        for (uint32_t i = threadIdx.x; i < 2 * kSlots; i += kThreads) s_sp[i] = g[i];
+        cls.tree = s_sp;
+        cls.sorted = s_sp + kSlots;
+        cls.m = nsplit[t.seg];
+    } else {
+        cls.mn = (K)segs[t.seg].min_ord;
+        cls.shift = shift;
+    }
+    for (uint32_t i = threadIdx.x; i < kHistCopies * kCols; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
+    uint32_t* mine = hist[(threadIdx.x >> 5) % kHistCopies];
     const K* p = src + t.begin;
 #pragma unroll 4
     for (uint32_t i = threadIdx.x; i < t.size; i += kThreads) {
-        const uint32_t b = classify(sp, m, (K)(p[i] ^ flip));
-        if (AHS_DCHECK(b < kCols, "count bucket", b)) atomicAdd(&hist[b], 1u);
+        const uint32_t b = cls((K)(p[i] ^ flip));
+        if (AHS_DCHECK(b < kCols, "count bucket", b)) atomicAdd(&mine[b], 1u);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < kCols; i += kThreads)
-        counts[(size_t)blockIdx.x * kCols + i] = hist[i];
+        counts[(size_t)blockIdx.x * kCols + i] = hist[0][i] + hist[1][i] + hist[2][i] + hist[3][i];
 }
 
 // Segmented column scan of the tiles x buckets count matrix, in three steps:
@@ -164,8 +212,10 @@ ss_scan_b(uint32_t* __restrict__ chunk_sum, const SegDesc* __restrict__ segs,
     }
     uint32_t total;
     const uint32_t base = block_exclusive_scan<kCols>(run, scratch, &total);
-    seg_tot[(size_t)blockIdx.x * kCols + j] = run;
-    seg_base[(size_t)blockIdx.x * kCols + j] = base;
+    if (seg_tot) {
+        seg_tot[(size_t)blockIdx.x * kCols + j] = run;
+        seg_base[(size_t)blockIdx.x * kCols + j] = base;
+    }
     for (uint32_t c = 0; c < sg.nchunks; ++c) chunk_sum[(size_t)(sg.first_chunk + c) * kCols + j] += base;
 }
 
@@ -185,7 +235,7 @@ ss_scan_c(uint32_t* __restrict__ counts, const ChunkDesc* __restrict__ chunks,
 
 template <typename K, bool VALS>
 struct ScatterSmem {
-    K sp[kMaxSplit + 1];
+    K sp[2 * kSlots];
     uint32_t warp_hist[kThreads / 32][kCols];
     uint32_t tile_count[kCols];
     uint32_t tile_start[kCols];
@@ -198,20 +248,31 @@ struct ScatterSmem {
 
 // Per tile: classify, rank stably by bucket, stage in bucket order, write
 // each bucket's run to its offset.
-template <typename K, bool VALS>
+template <typename K, bool VALS, int MODE>
 __global__ void __launch_bounds__(kThreads)
 ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __restrict__ vsrc,
            uint32_t* __restrict__ vdst, const TileDesc* __restrict__ tiles,
            const SegDesc* __restrict__ segs, const K* __restrict__ splitters,
-           const uint32_t* __restrict__ nsplit, K flip, const uint32_t* __restrict__ offs) {
+           const uint32_t* __restrict__ nsplit, K flip, uint32_t shift,
+           const uint32_t* __restrict__ offs) {
     constexpr int W = kThreads / 32;
     constexpr int WARP_ITEMS = 32 * kIpt;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem<K, VALS>& S = *reinterpret_cast<ScatterSmem<K, VALS>*>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const TileDesc t = tiles[blockIdx.x];
-    const uint32_t m = nsplit[t.seg];
-    for (uint32_t i = tid; i < m; i += kThreads) S.sp[i] = splitters[(size_t)t.seg * (kMaxSplit + 1) + i];
+    const SegDesc sg = segs[t.seg];
+    Classifier<K, MODE> cls{};
+    if constexpr (MODE == kSplit) {
+        const K* g = splitters + (size_t)t.seg * 2 * kSlots;
+        for (uint32_t i = tid; i < 2 * kSlots; i += kThreads) S.sp[i] = g[i];
+        cls.tree = S.sp;
+        cls.sorted = S.sp + kSlots;
+        cls.m = nsplit[t.seg];
+    } else {
+        cls.mn = (K)sg.min_ord;
+        cls.shift = shift;
+    }
     for (uint32_t i = tid; i < W * kCols; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
     __syncthreads();
 
@@ -224,7 +285,7 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
         const uint32_t q = wbase + 32 * i + lane;
         if (q < t.size) {
             key[i] = p[q];
-            b[i] = classify(S.sp, m, (K)(key[i] ^ flip));
+            b[i] = cls((K)(key[i] ^ flip));
         } else {
             key[i] = 0;
             b[i] = kCols;
@@ -242,8 +303,7 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
         rank[i] = old + __popc(peers & lt);
     }
     __syncthreads();
-    {
-        const uint32_t j = tid;   // kThreads == kCols
+    for (uint32_t j = tid; j < kCols; j += kThreads) {
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
@@ -278,7 +338,6 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
         }
     }
     __syncthreads();
-    const SegDesc sg = segs[t.seg];
     K* out = dst + sg.begin;
     uint32_t* vout = VALS ? vdst + sg.begin : nullptr;
     for (uint32_t j = tid; j < t.size; j += kThreads) {
@@ -291,85 +350,185 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-struct Carve {
-    void* ktmp;
-    uint32_t* vtmp;
-    uint32_t* counts;
-    uint32_t* chunk_sum;
-    uint32_t* seg_tot;
-    uint32_t* seg_base;
-    void* splitters;
-    uint32_t* nsplit;
-    SegDesc* segs;
-    TileDesc* tiles;
-    ChunkDesc* chunks;
-};
-
-struct Bounds {
-    uint64_t segs, tiles, chunks;
-};
-
-Bounds bounds_for(uint64_t n) {
-    Bounds b;
-    b.segs = n / (kBucketCap + 1) + 2;
-    b.tiles = 2 * (n / kTile) + b.segs + 2;
-    b.chunks = b.tiles / kChunkTiles + b.segs + 2;
-    return b;
-}
-
-size_t carve_bytes(uint64_t n, uint32_t kb, bool vals) {
-    const Bounds b = bounds_for(n);
-    return a256(n * kb) + (vals ? a256(n * 4) : 0) + a256(b.tiles * kCols * 4) +
-           a256(b.chunks * kCols * 4) + 2 * a256(b.segs * kCols * 4) +
-           a256(b.segs * (kMaxSplit + 1) * kb) + a256(b.segs * 4) + a256(b.segs * sizeof(SegDesc)) +
-           a256(b.tiles * sizeof(TileDesc)) + a256(b.chunks * sizeof(ChunkDesc)) + 256;
-}
-
-Carve carve(void* base, uint64_t n, uint32_t kb, bool vals) {
-    const Bounds b = bounds_for(n);
-    Carve c{};
-    char* p = static_cast<char*>(base);
-    auto take = [&](size_t bytes) { char* r = p; p += a256(bytes); return r; };
-    c.ktmp = take(n * kb);
-    c.vtmp = vals ? reinterpret_cast<uint32_t*>(take(n * 4)) : nullptr;
-    c.counts = reinterpret_cast<uint32_t*>(take(b.tiles * kCols * 4));
-    c.chunk_sum = reinterpret_cast<uint32_t*>(take(b.chunks * kCols * 4));
-    c.seg_tot = reinterpret_cast<uint32_t*>(take(b.segs * kCols * 4));
-    c.seg_base = reinterpret_cast<uint32_t*>(take(b.segs * kCols * 4));
-    c.splitters = take(b.segs * (kMaxSplit + 1) * kb);
-    c.nsplit = reinterpret_cast<uint32_t*>(take(b.segs * 4));
-    c.segs = reinterpret_cast<SegDesc*>(take(b.segs * sizeof(SegDesc)));
-    c.tiles = reinterpret_cast<TileDesc*>(take(b.tiles * sizeof(TileDesc)));
-    c.chunks = reinterpret_cast<ChunkDesc*>(take(b.chunks * sizeof(ChunkDesc)));
-    return c;
-}
-
 template <typename F>
 cudaError_t set_smem(F fn, size_t bytes) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-struct OpenSeg {
-    unsigned long long begin;
-    uint32_t size;
+// Host-built work lists and the per-level device metadata, which lives in the
+// context's auxiliary buffer sized for this level.
+struct Level {
+    std::vector<SegDesc> segs;
+    std::vector<TileDesc> tiles;
+    std::vector<ChunkDesc> chunks;
+    SegDesc* d_segs = nullptr;
+    TileDesc* d_tiles = nullptr;
+    ChunkDesc* d_chunks = nullptr;
+    uint32_t* counts = nullptr;
+    uint32_t* chunk_sum = nullptr;
+    uint32_t* seg_tot = nullptr;
+    uint32_t* seg_base = nullptr;
+    void* splitters = nullptr;
+    uint32_t* nsplit = nullptr;
 };
 
+void build_lists(const std::vector<SegRange>& open, Level& L) {
+    L.segs.clear();
+    L.tiles.clear();
+    L.chunks.clear();
+    for (uint32_t s = 0; s < open.size(); ++s) {
+        SegDesc sd{};
+        sd.begin = open[s].begin;
+        sd.size = open[s].size;
+        sd.min_ord = open[s].min_ord;
+        sd.first_chunk = (uint32_t)L.chunks.size();
+        const uint32_t nt = (uint32_t)ceil_div(sd.size, kTile);
+        const uint32_t t0 = (uint32_t)L.tiles.size();
+        for (uint32_t t = 0; t < nt; ++t) {
+            const uint32_t off = t * kTile;
+            L.tiles.push_back({sd.begin + off, std::min(kTile, sd.size - off), s});
+        }
+        for (uint32_t t = 0; t < nt; t += kChunkTiles)
+            L.chunks.push_back({t0 + t, std::min(kChunkTiles, nt - t), s, 0});
+        sd.nchunks = (uint32_t)L.chunks.size() - sd.first_chunk;
+        L.segs.push_back(sd);
+    }
+}
+
+// Carve the level's metadata in ctx->aux and upload the lists (synchronises
+// the stream so the pinned staging can be reused).
+ahs_status upload_level(ahs_ctx* ctx, Level& L, uint32_t key_bytes, bool split, cudaStream_t st) {
+    const size_t ns = L.segs.size(), nt = L.tiles.size(), nc = L.chunks.size();
+    const size_t b_segs = a256(ns * sizeof(SegDesc)), b_tiles = a256(nt * sizeof(TileDesc)),
+                 b_chunks = a256(nc * sizeof(ChunkDesc));
+    const size_t b_counts = a256(nt * kCols * 4), b_csum = a256(nc * kCols * 4),
+                 b_seg = a256(ns * kCols * 4), b_spl = split ? a256(ns * 2 * kSlots * key_bytes) : 0,
+                 b_ns = a256(ns * 4);
+    ahs_status rc = ensure_aux(ctx, b_segs + b_tiles + b_chunks + b_counts + b_csum + 2 * b_seg +
+                                        b_spl + b_ns);
+    if (rc == AHS_OK) rc = ensure_stage(ctx, b_segs + b_tiles + b_chunks);
+    if (rc != AHS_OK) return rc;
+    char* p = static_cast<char*>(ctx->aux);
+    L.d_segs = reinterpret_cast<SegDesc*>(p); p += b_segs;
+    L.d_tiles = reinterpret_cast<TileDesc*>(p); p += b_tiles;
+    L.d_chunks = reinterpret_cast<ChunkDesc*>(p); p += b_chunks;
+    L.counts = reinterpret_cast<uint32_t*>(p); p += b_counts;
+    L.chunk_sum = reinterpret_cast<uint32_t*>(p); p += b_csum;
+    L.seg_tot = reinterpret_cast<uint32_t*>(p); p += b_seg;
+    L.seg_base = reinterpret_cast<uint32_t*>(p); p += b_seg;
+    L.splitters = split ? p : nullptr; p += b_spl;
+    L.nsplit = reinterpret_cast<uint32_t*>(p);
+    char* hs = static_cast<char*>(ctx->h_stage);
+    std::memcpy(hs, L.segs.data(), ns * sizeof(SegDesc));
+    std::memcpy(hs + b_segs, L.tiles.data(), nt * sizeof(TileDesc));
+    std::memcpy(hs + b_segs + b_tiles, L.chunks.data(), nc * sizeof(ChunkDesc));
+    cudaError_t e = cudaMemcpyAsync(L.d_segs, hs, b_segs + b_tiles + b_chunks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(ctx, e);
+}
+
+// One stable partition of every segment of the level, src -> dst.
+template <typename K, bool VALS, int MODE>
+cudaError_t partition(const Level& L, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst,
+                      K flip, uint32_t level, uint32_t shift, bool totals, cudaStream_t st) {
+    const uint32_t ns = (uint32_t)L.segs.size(), nt = (uint32_t)L.tiles.size(),
+                   nc = (uint32_t)L.chunks.size();
+    uint64_t keys = 0;
+    for (const SegDesc& sd : L.segs) keys += sd.size;
+    K* spl = static_cast<K*>(L.splitters);
+    if constexpr (MODE == kSplit) {
+        TraceScope ts("sample_splitters", ns, st);
+        ss_sample<K><<<ns, kThreads, sizeof(BlockSortSmem<K, false, kThreads, kIpt>), st>>>(
+            src, L.d_segs, level, flip, spl, L.nsplit);
+    }
+    {
+        TraceScope ts(MODE == kSplit ? "sample_count" : "segradix_count", keys, st);
+        ss_count<K, MODE><<<nt, kThreads, 0, st>>>(src, L.d_tiles, L.d_segs, spl, L.nsplit, flip,
+                                                   shift, L.counts);
+    }
+    {
+        TraceScope ts(MODE == kSplit ? "sample_scan" : "segradix_scan", nt, st);
+        ss_scan_a<<<nc, kCols, 0, st>>>(L.counts, L.d_chunks, L.chunk_sum);
+        ss_scan_b<<<ns, kCols, 0, st>>>(L.chunk_sum, L.d_segs, totals ? L.seg_tot : nullptr,
+                                        L.seg_base);
+        ss_scan_c<<<nc, kCols, 0, st>>>(L.counts, L.d_chunks, L.chunk_sum);
+    }
+    {
+        TraceScope ts(MODE == kSplit ? "sample_scatter" : "segradix_scatter", keys, st);
+        ss_scatter<K, VALS, MODE><<<nt, kThreads, sizeof(ScatterSmem<K, VALS>), st>>>(
+            src, dst, vsrc, vdst, L.d_tiles, L.d_segs, spl, L.nsplit, flip, shift, L.counts);
+    }
+    return cudaGetLastError();
+}
+
 template <typename K, bool VALS>
-ahs_status samplesort_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uint32_t* vout,
-                        uint64_t n, K flip, void* scratch, cudaStream_t st, uint32_t* levels_out,
-                        uint32_t* buckets_out) {
-    const Carve c = carve(scratch, n, sizeof(K), VALS);
-    K* ktmp = static_cast<K*>(c.ktmp);
-    cudaError_t e;
-    e = set_smem(ss_sample<K>, sizeof(BlockSortSmem<K, false, kThreads, kIpt>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS>, sizeof(ScatterSmem<K, VALS>));
+cudaError_t set_attrs() {
+    cudaError_t e = set_smem(ss_sample<K>, sizeof(BlockSortSmem<K, false, kThreads, kIpt>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kSplit>, sizeof(ScatterSmem<K, VALS>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kDigit>, sizeof(ScatterSmem<K, VALS>));
+    return e;
+}
+
+// Upload a final-bucket list to the auxiliary buffer and run the bucket
+// sorts (one launch per size class); synchronises before returning so the
+// pinned staging can be reused.
+ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, const void* ktmp,
+                          const void* kout, const void* kin, const uint32_t* vtmp, uint32_t* vout,
+                          const uint32_t* vin, KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
+    std::vector<FinalBucket> cls[3];
+    uint32_t nsorted = 0;
+    for (const FinalBucket& f : finals) {
+        cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
+        nsorted += f.sort;
+    }
+    if (sorted) *sorted = nsorted;
+    const size_t nf = finals.size();
+    if (nf == 0) return AHS_OK;
+    ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
+    if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
+    if (rc != AHS_OK) return rc;
+    FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
+    FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
+    const FinalBucket* lists[3];
+    uint32_t counts[3];
+    uint64_t keys[3];
+    size_t at = 0;
+    for (int k = 0; k < 3; ++k) {
+        std::memcpy(hf + at, cls[k].data(), cls[k].size() * sizeof(FinalBucket));
+        lists[k] = df + at;
+        counts[k] = (uint32_t)cls[k].size();
+        keys[k] = 0;
+        for (const FinalBucket& f : cls[k]) keys[k] += f.size;
+        at += cls[k].size();
+    }
+    cudaError_t e = cudaMemcpyAsync(df, hf, nf * sizeof(FinalBucket), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
+                                 vtmp, vout, vin, vout, kd, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(ctx, e);
+}
+
+template <typename K, bool VALS>
+ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uint32_t* vout,
+                     uint64_t n_total, const std::vector<SegRange>& segs,
+                     const std::vector<SegRange>& extra, K flip, void* scratch, cudaStream_t st,
+                     uint32_t* levels_out, uint32_t* buckets_out) {
+    char* p = static_cast<char*>(scratch);
+    K* ktmp = reinterpret_cast<K*>(p);
+    uint32_t* vtmp = VALS ? reinterpret_cast<uint32_t*>(p + a256(n_total * sizeof(K))) : nullptr;
+    cudaError_t e = set_attrs<K, VALS>();
     if (e != cudaSuccess) return cuda_status(ctx, e);
 
-    std::vector<OpenSeg> open{{0ull, (uint32_t)n}};
     std::vector<FinalBucket> finals;
-    std::vector<SegDesc> hsegs;
-    std::vector<TileDesc> htiles;
-    std::vector<ChunkDesc> hchunks;
+    for (const SegRange& x : extra)
+        finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1 ? 1 : 0), 0});
+    std::vector<SegRange> open;
+    for (const SegRange& x : segs) {
+        if (x.size <= kBucketCap) finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1), 0});
+        else open.push_back(x);
+    }
+    Level L;
     uint32_t level = 0;
     while (!open.empty()) {
         if (level >= kMaxLevels) return AHS_ERR_UNIMPLEMENTED;
@@ -377,141 +536,124 @@ ahs_status samplesort_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin
         // Level 1 reads the input; odd levels write the temporary buffer, even
         // levels the output, so a level never overwrites its own source.
         const K* src = level == 1 ? kin : (level % 2 == 0 ? ktmp : kout);
-        const uint32_t* vsrc = level == 1 ? vin : (level % 2 == 0 ? c.vtmp : vout);
+        const uint32_t* vsrc = level == 1 ? vin : (level % 2 == 0 ? vtmp : vout);
         K* dst = (level % 2 == 1) ? ktmp : kout;
-        uint32_t* vdst = (level % 2 == 1) ? c.vtmp : vout;
+        uint32_t* vdst = (level % 2 == 1) ? vtmp : vout;
         const uint8_t where = (level % 2 == 1) ? 0 : 1;
-
-        hsegs.clear();
-        htiles.clear();
-        hchunks.clear();
-        for (uint32_t s = 0; s < open.size(); ++s) {
-            SegDesc sd{};
-            sd.begin = open[s].begin;
-            sd.size = open[s].size;
-            sd.first_chunk = (uint32_t)hchunks.size();
-            const uint32_t nt = (uint32_t)ceil_div(sd.size, kTile);
-            const uint32_t t0 = (uint32_t)htiles.size();
-            for (uint32_t t = 0; t < nt; ++t) {
-                const uint32_t off = t * kTile;
-                htiles.push_back({sd.begin + off, std::min(kTile, sd.size - off), s});
-            }
-            for (uint32_t t = 0; t < nt; t += kChunkTiles)
-                hchunks.push_back({t0 + t, std::min(kChunkTiles, nt - t), s, 0});
-            sd.nchunks = (uint32_t)hchunks.size() - sd.first_chunk;
-            hsegs.push_back(sd);
-        }
-        const size_t bseg = hsegs.size() * sizeof(SegDesc), btile = htiles.size() * sizeof(TileDesc),
-                     bchunk = hchunks.size() * sizeof(ChunkDesc);
-        const size_t bread = hsegs.size() * kCols * 4;
-        ahs_status rc = ensure_stage(ctx, std::max(bseg + btile + bchunk, 2 * bread));
+        build_lists(open, L);
+        ahs_status rc = upload_level(ctx, L, sizeof(K), true, st);
+        if (rc != AHS_OK) return rc;
+        e = partition<K, VALS, kSplit>(L, src, dst, vsrc, vdst, flip, level, 0, true, st);
+        const size_t ns = L.segs.size(), bread = ns * kCols * 4;
+        if (e == cudaSuccess) rc = ensure_stage(ctx, 2 * bread);
         if (rc != AHS_OK) return rc;
         char* hs = static_cast<char*>(ctx->h_stage);
-        std::memcpy(hs, hsegs.data(), bseg);
-        std::memcpy(hs + bseg, htiles.data(), btile);
-        std::memcpy(hs + bseg + btile, hchunks.data(), bchunk);
-        e = cudaMemcpyAsync(c.segs, hs, bseg, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c.tiles, hs + bseg, btile, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c.chunks, hs + bseg + btile, bchunk, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_status(ctx, e);
-
-        K* spl = static_cast<K*>(c.splitters);
-        const uint32_t ns = (uint32_t)hsegs.size(), nt = (uint32_t)htiles.size(),
-                       nc = (uint32_t)hchunks.size();
-        uint64_t level_keys = 0;
-        for (const SegDesc& sd : hsegs) level_keys += sd.size;
-        {
-            TraceScope ts("sample_splitters", ns, st);
-            ss_sample<K><<<ns, kThreads, sizeof(BlockSortSmem<K, false, kThreads, kIpt>), st>>>(
-                src, c.segs, level, flip, spl, c.nsplit);
-        }
-        {
-            TraceScope ts("sample_count", level_keys, st);
-            ss_count<K><<<nt, kThreads, 0, st>>>(src, c.tiles, spl, c.nsplit, flip, c.counts);
-        }
-        {
-            TraceScope ts("sample_scan", nt, st);
-            ss_scan_a<<<nc, kCols, 0, st>>>(c.counts, c.chunks, c.chunk_sum);
-            ss_scan_b<<<ns, kCols, 0, st>>>(c.chunk_sum, c.segs, c.seg_tot, c.seg_base);
-            ss_scan_c<<<nc, kCols, 0, st>>>(c.counts, c.chunks, c.chunk_sum);
-        }
-        {
-            TraceScope ts("sample_scatter", level_keys, st);
-            ss_scatter<K, VALS><<<nt, kThreads, sizeof(ScatterSmem<K, VALS>), st>>>(
-                src, dst, vsrc, vdst, c.tiles, c.segs, spl, c.nsplit, flip, c.counts);
-        }
-        e = cudaGetLastError();
-        // The stage buffer is reused for the readback: wait for the uploads.
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, c.seg_tot, bread, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hs + bread, c.seg_base, bread, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, L.seg_tot, bread, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs + bread, L.seg_base, bread, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(ctx, e);
-
         const uint32_t* tot = reinterpret_cast<const uint32_t*>(hs);
         const uint32_t* base = reinterpret_cast<const uint32_t*>(hs + bread);
-        std::vector<OpenSeg> next;
+        std::vector<SegRange> next;
         for (uint32_t s = 0; s < ns; ++s) {
             for (uint32_t j = 0; j < kCols; ++j) {
                 const uint32_t sz = tot[(size_t)s * kCols + j];
                 if (sz == 0) continue;
-                const unsigned long long b0 = hsegs[s].begin + base[(size_t)s * kCols + j];
+                const unsigned long long b0 = L.segs[s].begin + base[(size_t)s * kCols + j];
                 const bool equal = (j & 1u) != 0;
                 if (equal || sz == 1) {
                     if (where == 0) finals.push_back({b0, sz, where, 0, 0});   // copy to output
                 } else if (sz <= kBucketCap) {
                     finals.push_back({b0, sz, where, 1, 0});
                 } else {
-                    next.push_back({b0, sz});
+                    next.push_back({b0, sz, 0});
                 }
             }
         }
         open.swap(next);
     }
-
-    // Bucket sorts, one launch per size class.
-    std::vector<FinalBucket> cls[3];
-    uint32_t sorted_buckets = 0;
-    for (const FinalBucket& f : finals) {
-        cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
-        sorted_buckets += f.sort;
-    }
-    const size_t nf = finals.size();
-    if (nf) {
-        ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
-        if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
-        if (rc != AHS_OK) return rc;
-        FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
-        FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
-        const FinalBucket* lists[3];
-        uint32_t counts[3];
-        uint64_t keys[3];
-        size_t at = 0;
-        for (int k = 0; k < 3; ++k) {
-            std::memcpy(hf + at, cls[k].data(), cls[k].size() * sizeof(FinalBucket));
-            lists[k] = df + at;
-            counts[k] = (uint32_t)cls[k].size();
-            keys[k] = 0;
-            for (const FinalBucket& f : cls[k]) keys[k] += f.size;
-            at += cls[k].size();
-        }
-        e = cudaMemcpyAsync(df, hf, nf * sizeof(FinalBucket), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kout, c.vtmp, vout, vout,
-                                     KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st);
-        // The pinned stage holds the list until the copy has been consumed.
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_status(ctx, e);
-    }
     *levels_out = level;
-    *buckets_out = sorted_buckets;
+    return finish_buckets(ctx, finals, ktmp, kout, kin, vtmp, vout, vin,
+                          KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+}
+
+template <typename K, bool VALS>
+ahs_status radix_segs_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uint32_t* vout,
+                        uint64_t n_total, const std::vector<SegRange>& segs, uint32_t passes,
+                        K flip, void* scratch, cudaStream_t st) {
+    if (segs.empty() || passes == 0) return AHS_OK;
+    char* p = static_cast<char*>(scratch);
+    K* ktmp = reinterpret_cast<K*>(p);
+    uint32_t* vtmp = VALS ? reinterpret_cast<uint32_t*>(p + a256(n_total * sizeof(K))) : nullptr;
+    cudaError_t e = set_attrs<K, VALS>();
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    Level L;
+    build_lists(segs, L);
+    ahs_status rc = upload_level(ctx, L, sizeof(K), false, st);
+    if (rc != AHS_OK) return rc;
+    // The last pass writes kout: odd pass counts start kin -> kout.
+    const K* src = kin;
+    const uint32_t* vsrc = vin;
+    for (uint32_t q = 0; q < passes; ++q) {
+        const bool to_out = ((passes - 1 - q) % 2) == 0;
+        K* dst = to_out ? kout : ktmp;
+        uint32_t* vdst = to_out ? vout : vtmp;
+        e = partition<K, VALS, kDigit>(L, src, dst, vsrc, vdst, flip, 0, 8 * q, false, st);
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+        src = dst;
+        vsrc = vdst;
+    }
     return AHS_OK;
 }
 
 }  // namespace
 
 size_t samplesort_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals) {
-    return carve_bytes(n, key_bytes, has_vals);
+    return segsort_scratch_bytes(n, 1, key_bytes, has_vals);
+}
+
+size_t segsort_scratch_bytes(uint64_t n_total, uint64_t, uint32_t key_bytes, bool vals) {
+    return a256(n_total * key_bytes) + (vals ? a256(n_total * 4) : 0) + 256;
+}
+
+ahs_status run_segmented_general(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
+                                 uint32_t* vout, uint64_t n_total, const std::vector<SegRange>& segs,
+                                 const std::vector<SegRange>& extra, KeyDesc kd, void* scratch,
+                                 cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
+    *levels_out = 0;
+    *buckets_out = 0;
+    const bool v = vin != nullptr;
+    if (kd.bytes == 4) {
+        const uint32_t f = (uint32_t)kd.flip;
+        return v ? general_t<uint32_t, true>(ctx, (const uint32_t*)kin, (uint32_t*)kout, vin, vout, n_total, segs, extra, f, scratch, st, levels_out, buckets_out)
+                 : general_t<uint32_t, false>(ctx, (const uint32_t*)kin, (uint32_t*)kout, nullptr, nullptr, n_total, segs, extra, f, scratch, st, levels_out, buckets_out);
+    }
+    return v ? general_t<uint64_t, true>(ctx, (const uint64_t*)kin, (uint64_t*)kout, vin, vout, n_total, segs, extra, kd.flip, scratch, st, levels_out, buckets_out)
+             : general_t<uint64_t, false>(ctx, (const uint64_t*)kin, (uint64_t*)kout, nullptr, nullptr, n_total, segs, extra, kd.flip, scratch, st, levels_out, buckets_out);
+}
+
+ahs_status run_segmented_radix(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
+                               uint32_t* vout, uint64_t n_total, const std::vector<SegRange>& segs,
+                               uint32_t passes, KeyDesc kd, void* scratch, cudaStream_t st) {
+    const bool v = vin != nullptr;
+    if (kd.bytes == 4) {
+        const uint32_t f = (uint32_t)kd.flip;
+        return v ? radix_segs_t<uint32_t, true>(ctx, (const uint32_t*)kin, (uint32_t*)kout, vin, vout, n_total, segs, passes, f, scratch, st)
+                 : radix_segs_t<uint32_t, false>(ctx, (const uint32_t*)kin, (uint32_t*)kout, nullptr, nullptr, n_total, segs, passes, f, scratch, st);
+    }
+    return v ? radix_segs_t<uint64_t, true>(ctx, (const uint64_t*)kin, (uint64_t*)kout, vin, vout, n_total, segs, passes, kd.flip, scratch, st)
+             : radix_segs_t<uint64_t, false>(ctx, (const uint64_t*)kin, (uint64_t*)kout, nullptr, nullptr, n_total, segs, passes, kd.flip, scratch, st);
+}
+
+ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
+                              uint32_t* vout, const std::vector<SegRange>& sort_segs,
+                              const std::vector<SegRange>& copy_segs, KeyDesc kd, cudaStream_t st) {
+    std::vector<FinalBucket> finals;
+    finals.reserve(sort_segs.size() + copy_segs.size());
+    for (const SegRange& x : sort_segs) finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1), 0});
+    for (const SegRange& x : copy_segs) finals.push_back({x.begin, x.size, 2, 0, 0});
+    // No temporary buffer is involved: every bucket reads kin and writes kout.
+    return finish_buckets(ctx, finals, kout, kout, kin, vout, vout, vin, kd, st, nullptr);
 }
 
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
@@ -523,14 +665,9 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
         *buckets_out = 1;
         return cuda_status(ctx, launch_blocksort_single(kin, kout, vin, vout, n, kd, st));
     }
-    const bool v = vin != nullptr;
-    if (kd.bytes == 4) {
-        const uint32_t f = (uint32_t)kd.flip;
-        return v ? samplesort_t<uint32_t, true>(ctx, (const uint32_t*)kin, (uint32_t*)kout, vin, vout, n, f, scratch, st, levels_out, buckets_out)
-                 : samplesort_t<uint32_t, false>(ctx, (const uint32_t*)kin, (uint32_t*)kout, nullptr, nullptr, n, f, scratch, st, levels_out, buckets_out);
-    }
-    return v ? samplesort_t<uint64_t, true>(ctx, (const uint64_t*)kin, (uint64_t*)kout, vin, vout, n, kd.flip, scratch, st, levels_out, buckets_out)
-             : samplesort_t<uint64_t, false>(ctx, (const uint64_t*)kin, (uint64_t*)kout, nullptr, nullptr, n, kd.flip, scratch, st, levels_out, buckets_out);
+    std::vector<SegRange> segs{{0ull, (uint32_t)n, 0ull}};
+    return run_segmented_general(ctx, kin, kout, vin, vout, n, segs, {}, kd, scratch, st,
+                                 levels_out, buckets_out);
 }
 
 }  // namespace ahs

@@ -14,7 +14,7 @@ constexpr uint32_t kBucketCap = 8192;
 constexpr uint32_t kBucketClassCap[3] = {1024, 4096, 8192};
 
 // A bucket that leaves the partition levels: its keys sit in buffer `where`
-// (0: temporary, 1: the output) at [begin, begin + size).
+// (0: temporary, 1: the output, 2: the input) at [begin, begin + size).
 struct FinalBucket {
     unsigned long long begin;
     uint32_t size;
@@ -26,8 +26,9 @@ static_assert(sizeof(FinalBucket) == 16, "FinalBucket layout");
 
 uint32_t bucket_class(uint32_t size);
 cudaError_t launch_bucket_finish(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                                 const uint64_t keys[3], const void* buf0, const void* buf1, void* out,
-                                 const uint32_t* vbuf0, const uint32_t* vbuf1, uint32_t* vout,
+                                 const uint64_t keys[3], const void* buf0, const void* buf1,
+                                 const void* buf2, void* out, const uint32_t* vbuf0,
+                                 const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
                                  KeyDesc kd, cudaStream_t st);
 
 }  // namespace ahs

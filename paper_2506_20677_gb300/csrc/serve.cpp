@@ -1,16 +1,333 @@
-// Serving loop and batched sorts (filled in below).
+// Serving loop with continuous batching.
+//
+// Requests (device keys, n, type) are submitted from any thread and admitted
+// against an HBM budget: a request reserves the device memory its sort needs
+// (staging plus temporary buffers) and releases it on completion; one that
+// could never fit is refused at submission.  Two worker lanes run on their own
+// streams and contexts, so their work overlaps on the GPU:
+//   - the batch lane folds every admitted request below the large-request
+//     cutoff into one batched launch (gathered into a staging arena, sorted
+//     by the batched path, scattered back), and keeps folding new arrivals
+//     into the next batch while one is on the GPU;
+//   - the large lane sorts big requests one by one with the single-array path.
+// Latency is measured on the host from submission to completion.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "ctx.h"
+#include "internal.h"
+
+namespace ahs {
+ahs_status run_batch(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
+                     const uint64_t* offs, uint32_t n_seg, KeyDesc kd, cudaStream_t st,
+                     ahs_batch_info_t* info);
+
+namespace {
+using clock = std::chrono::steady_clock;
+
+// Requests at or above this size go to the large lane.
+constexpr uint64_t kLargeKeys = 1ull << 22;
+// A batch folds requests up to this many keys (bounded arena).
+constexpr uint64_t kBatchKeys = 1ull << 27;
+
+struct Request {
+    uint64_t ticket;
+    ahs_request_t req;
+    uint64_t reserve;
+    clock::time_point submitted, admitted;
+    bool large;
+};
+
+struct Done {
+    ahs_result_t res;
+};
+
+uint64_t reserve_for(const ahs_request_t& r) {
+    const uint64_t w = (r.type == AHS_U32 || r.type == AHS_I32) ? 4 : 8;
+    // Temporary keys + partition metadata (about n/4 bytes) + a fixed part;
+    // batched requests also occupy the staging arena (in + out).
+    return r.n * w * 3 + r.n / 4 + (1ull << 20);
+}
+
+}  // namespace
+
+struct ServeState {
+    ahs_serve_config_t cfg{};
+    ahs_ctx* batch_ctx = nullptr;   // own workspace per lane
+    ahs_ctx* large_ctx = nullptr;
+    cudaStream_t batch_stream = nullptr, large_stream = nullptr;
+    int device = 0;
+
+    std::mutex mu;
+    std::condition_variable work_cv, done_cv;
+    std::deque<Request> queue;            // submitted, waiting for admission
+    std::deque<Request> batch_ready, large_ready;
+    std::unordered_map<uint64_t, Done> done;
+    uint64_t next_ticket = 1;
+    uint64_t reserved = 0, peak_reserved = 0;
+    uint32_t inflight = 0;
+    bool stopping = false;
+
+    std::vector<double> latencies;
+    uint64_t completed = 0, keys = 0, batches = 0;
+
+    // Staging arena of the batch lane (device), grown on demand.
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::thread batch_thread, large_thread;
+
+    // Move queued requests into the lanes while budget and slots allow (FIFO).
+    void admit_locked() {
+        while (!queue.empty()) {
+            Request& r = queue.front();
+            if (inflight >= cfg.max_inflight || reserved + r.reserve > cfg.budget_bytes) break;
+            reserved += r.reserve;
+            peak_reserved = std::max(peak_reserved, reserved);
+            ++inflight;
+            r.admitted = clock::now();
+            (r.large ? large_ready : batch_ready).push_back(r);
+            queue.pop_front();
+        }
+    }
+
+    void finish_locked(const Request& r, ahs_status st, ahs_strategy strategy) {
+        const auto now = clock::now();
+        Done d{};
+        d.res.status = st;
+        d.res.strategy = strategy;
+        d.res.latency_ms = std::chrono::duration<double, std::milli>(now - r.submitted).count();
+        d.res.queue_ms = std::chrono::duration<double, std::milli>(r.admitted - r.submitted).count();
+        done[r.ticket] = d;
+        reserved -= r.reserve;
+        --inflight;
+        if (st == AHS_OK) {
+            latencies.push_back(d.res.latency_ms);
+            ++completed;
+            keys += r.req.n;
+        }
+        admit_locked();
+    }
+
+    void large_loop() {
+        cudaSetDevice(device);
+        for (;;) {
+            Request r;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                work_cv.wait(lk, [&] { return stopping || !large_ready.empty(); });
+                if (large_ready.empty()) return;
+                r = large_ready.front();
+                large_ready.pop_front();
+            }
+            ahs_sort_info_t info;
+            ahs_status st = ahs_sort(large_ctx, r.req.d_keys_in, r.req.d_keys_out, nullptr, nullptr,
+                                     r.req.n, r.req.type, AHS_AUTO, large_stream, &info);
+            std::lock_guard<std::mutex> lk(mu);
+            finish_locked(r, st, info.strategy);
+            done_cv.notify_all();
+            work_cv.notify_all();
+        }
+    }
+
+    void batch_loop() {
+        cudaSetDevice(device);
+        for (;;) {
+            std::vector<Request> batch;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                work_cv.wait_for(lk, std::chrono::microseconds(cfg.tick_us ? cfg.tick_us : 200),
+                                 [&] { return stopping || !batch_ready.empty(); });
+                if (batch_ready.empty()) {
+                    if (stopping) return;
+                    continue;
+                }
+                // Fold every ready request of one key type, up to the arena bound.
+                uint64_t nk = 0;
+                const ahs_key_type t = batch_ready.front().req.type;
+                for (auto it = batch_ready.begin(); it != batch_ready.end();) {
+                    if (it->req.type == t && (batch.empty() || nk + it->req.n <= kBatchKeys)) {
+                        nk += it->req.n;
+                        batch.push_back(*it);
+                        it = batch_ready.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            const ahs_status st = run_one_batch(batch);
+            std::lock_guard<std::mutex> lk(mu);
+            ++batches;
+            for (const Request& r : batch) finish_locked(r, st, AHS_AUTO);
+            done_cv.notify_all();
+            work_cv.notify_all();
+        }
+    }
+
+    ahs_status run_one_batch(const std::vector<Request>& batch) {
+        const KeyDesc kd = key_desc(batch[0].req.type);
+        std::vector<uint64_t> offs(batch.size() + 1, 0);
+        for (size_t i = 0; i < batch.size(); ++i) offs[i + 1] = offs[i] + batch[i].req.n;
+        const uint64_t n = offs.back();
+        const size_t need = 2 * ((n * kd.bytes + 255) & ~size_t(255));
+        if (need > arena_bytes) {
+            if (arena) cudaFree(arena);
+            arena = nullptr;
+            arena_bytes = 0;
+            if (cudaMalloc(&arena, need + need / 2) != cudaSuccess) {
+                cudaGetLastError();
+                return AHS_ERR_OOM;
+            }
+            arena_bytes = need + need / 2;
+        }
+        char* in = static_cast<char*>(arena);
+        char* out = in + ((n * kd.bytes + 255) & ~size_t(255));
+        cudaError_t e = cudaSuccess;
+        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i)
+            e = launch_copy32(in + offs[i] * kd.bytes, batch[i].req.d_keys_in,
+                              batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
+        if (e != cudaSuccess) return cuda_status(batch_ctx, e);
+        ahs_batch_info_t info;
+        ahs_status st = run_batch(batch_ctx, in, out, nullptr, nullptr, offs.data(),
+                                  (uint32_t)batch.size(), kd, batch_stream, &info);
+        if (st != AHS_OK) return st;
+        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i)
+            e = launch_copy32(batch[i].req.d_keys_out, out + offs[i] * kd.bytes,
+                              batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(batch_stream);
+        return cuda_status(batch_ctx, e);
+    }
+};
+
+}  // namespace ahs
+
+using ahs::ServeState;
 
 extern "C" {
 
-ahs_status ahs_sort_batch(ahs_ctx*, const void*, void*, const uint32_t*, uint32_t*, const uint64_t*,
-                          uint32_t, ahs_key_type, void*, ahs_batch_info_t*) {
-    return AHS_ERR_UNIMPLEMENTED;
+ahs_status ahs_serve_start(ahs_ctx* ctx, const ahs_serve_config_t* cfg) {
+    if (!ctx || !cfg || cfg->budget_bytes == 0 || cfg->max_inflight == 0) return AHS_ERR_INVALID_ARG;
+    if (ctx->serve) return AHS_ERR_INVALID_ARG;
+    auto* s = new (std::nothrow) ServeState();
+    if (!s) return AHS_ERR_OOM;
+    s->cfg = *cfg;
+    s->device = ctx->device;
+    ahs_config_t c = ctx->cfg;
+    c.timing = 0;
+    ahs_status rc = ahs_create(&s->batch_ctx, &c);
+    if (rc == AHS_OK) rc = ahs_create(&s->large_ctx, &c);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (rc == AHS_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->batch_stream, cudaStreamNonBlocking);
+    if (rc == AHS_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->large_stream, cudaStreamNonBlocking);
+    if (rc == AHS_OK && e != cudaSuccess) rc = ahs::cuda_status(ctx, e);
+    if (rc != AHS_OK) {
+        if (s->batch_ctx) ahs_destroy(s->batch_ctx);
+        if (s->large_ctx) ahs_destroy(s->large_ctx);
+        if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
+        if (s->large_stream) cudaStreamDestroy(s->large_stream);
+        delete s;
+        return rc;
+    }
+    ctx->serve = s;
+    s->batch_thread = std::thread([s] { s->batch_loop(); });
+    s->large_thread = std::thread([s] { s->large_loop(); });
+    return AHS_OK;
 }
-ahs_status ahs_serve_start(ahs_ctx*, const ahs_serve_config_t*) { return AHS_ERR_UNIMPLEMENTED; }
-ahs_status ahs_serve_submit(ahs_ctx*, const ahs_request_t*, uint64_t*) { return AHS_ERR_UNIMPLEMENTED; }
-ahs_status ahs_serve_poll(ahs_ctx*, uint64_t, int32_t, ahs_result_t*) { return AHS_ERR_UNIMPLEMENTED; }
-ahs_status ahs_serve_stats(ahs_ctx*, ahs_serve_stats_t*) { return AHS_ERR_UNIMPLEMENTED; }
-ahs_status ahs_serve_stop(ahs_ctx*) { return AHS_OK; }
 
+ahs_status ahs_serve_submit(ahs_ctx* ctx, const ahs_request_t* req, uint64_t* ticket) {
+    if (!ctx || !req || !ticket) return AHS_ERR_INVALID_ARG;
+    ServeState* s = ctx->serve;
+    if (!s) return AHS_ERR_INVALID_ARG;
+    if (req->type < AHS_U32 || req->type > AHS_I64) return AHS_ERR_DTYPE;
+    if (req->n && (!req->d_keys_in || !req->d_keys_out)) return AHS_ERR_INVALID_ARG;
+    ahs::Request r{};
+    r.req = *req;
+    r.reserve = ahs::reserve_for(*req);
+    r.large = req->n >= ahs::kLargeKeys;
+    r.submitted = ahs::clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return AHS_ERR_INVALID_ARG;
+    if (r.reserve > s->cfg.budget_bytes) return AHS_ERR_BUDGET;
+    r.ticket = s->next_ticket++;
+    *ticket = r.ticket;
+    if (req->n == 0) {
+        ahs::Done d{};
+        d.res.status = AHS_OK;
+        d.res.strategy = AHS_IDENTITY;
+        s->done[r.ticket] = d;
+        return AHS_OK;
+    }
+    s->queue.push_back(r);
+    s->admit_locked();
+    s->work_cv.notify_all();
+    return AHS_OK;
 }
+
+ahs_status ahs_serve_poll(ahs_ctx* ctx, uint64_t ticket, int32_t timeout_ms, ahs_result_t* out) {
+    if (!ctx || !out) return AHS_ERR_INVALID_ARG;
+    ServeState* s = ctx->serve;
+    if (!s) return AHS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (ticket == 0 || ticket >= s->next_ticket) return AHS_ERR_NOT_FOUND;
+    auto ready = [&] { return s->done.count(ticket) != 0; };
+    if (!ready() && timeout_ms > 0)
+        s->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) return AHS_ERR_AGAIN;
+    *out = it->second.res;
+    s->done.erase(it);
+    return AHS_OK;
+}
+
+ahs_status ahs_serve_stats(ahs_ctx* ctx, ahs_serve_stats_t* out) {
+    if (!ctx || !out || !ctx->serve) return AHS_ERR_INVALID_ARG;
+    ServeState* s = ctx->serve;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = s->completed;
+    out->keys = s->keys;
+    out->peak_reserved_bytes = s->peak_reserved;
+    out->batches = s->batches;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    return AHS_OK;
+}
+
+ahs_status ahs_serve_stop(ahs_ctx* ctx) {
+    if (!ctx) return AHS_ERR_INVALID_ARG;
+    ServeState* s = ctx->serve;
+    if (!s) return AHS_OK;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        // Drain: wait until everything submitted has completed.
+        s->done_cv.wait(lk, [&] { return s->queue.empty() && s->inflight == 0; });
+        s->stopping = true;
+    }
+    s->work_cv.notify_all();
+    if (s->batch_thread.joinable()) s->batch_thread.join();
+    if (s->large_thread.joinable()) s->large_thread.join();
+    cudaSetDevice(s->device);
+    if (s->arena) cudaFree(s->arena);
+    cudaStreamDestroy(s->batch_stream);
+    cudaStreamDestroy(s->large_stream);
+    ahs_destroy(s->batch_ctx);
+    ahs_destroy(s->large_ctx);
+    delete s;
+    ctx->serve = nullptr;
+    return AHS_OK;
+}
+
+}  // extern "C"
