@@ -33,7 +33,8 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
     table = {
         "features_minmax": w, "features_histogram": w, "counting_fill": w,
         "radix_digit_hist": w, "radix_onesweep": 2 * (w + v), "sample_count": w,
-        "sample_scatter": 2 * (w + v), "bucket_sort_1k": 2 * (w + v),
+        "sample_scatter": 2 * (w + v), "bucket_sort_1k": 2 * (w + v), "bucket_sort_2k": 2 * (w + v),
+        "segradix_count": w, "segradix_scatter": 2 * (w + v),
         "bucket_sort_4k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
         "blocksort_single": 2 * (w + v), "copy": 8,
     }
@@ -120,9 +121,17 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        # Replicas exchange only a barrier and one timing value.
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
+
+
+def job_value(world: int, keys_per_step: int, steps: int, ms_max: float) -> float:
+    """Whole-job Gkeys/s of weakly scaled replicas: every rank sorts its own
+    keys_per_step keys per step; the job time is the slowest rank's."""
+    return world * keys_per_step * steps / (ms_max / 1e3) / 1e9
 
 
 def barrier(world):
@@ -136,7 +145,8 @@ def max_over_ranks(world, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -253,7 +263,7 @@ def run_ours(args, world, rank, local):
     ms_total = t_start.elapsed_time(t_end)
     ms_total = max_over_ranks(world, ms_total)
     keys_per_step = len(VARIANTS) * n
-    value = world * keys_per_step * args.steps / (ms_total / 1e3) / 1e9
+    value = job_value(world, keys_per_step, args.steps, ms_total)
 
     # Per-variant p50 / p99 and per-kernel totals.
     import collections
@@ -309,7 +319,12 @@ def run_ours(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
-    e2e_value = world * keys_per_step * args.steps / (e2e_ms / 1e3) / 1e9
+    e2e_value = job_value(world, keys_per_step, args.steps, e2e_ms)
+
+    batched = served = None
+    if not args.no_extras:
+        batched = run_batched(ctx, args.batch_segments, 3)
+        served = run_served(local, args.serve_load, args.serve_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -342,9 +357,145 @@ def run_ours(args, world, rank, local):
                     "h2d_bytes_per_step": keys_per_step * 4, "d2h_bytes_per_step": keys_per_step * 4},
             "clocks": clk,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
+    """Config 4's recipe with n_seg segments: the batched call against a loop
+    of per-array calls on the same stream, same keys."""
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    from gen import device as gdev
+    keys, offs, lengths, types = gdev.config4(n_seg=n_seg)
+    out = torch.empty_like(keys)
+    total = int(offs[-1])
+    offs_l = offs.tolist()
+    ctx.sort_batch(keys, offs_l, out=out, key_type=ahs.AHS_U32)        # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    info = None
+    for _ in range(steps):
+        e0.record()
+        _, _, info = ctx.sort_batch(keys, offs_l, out=out, key_type=ahs.AHS_U32)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    res = {"segments": n_seg, "keys": total, "batched_ms_p50": round(statistics.median(times), 3),
+           "batched_gkeys_s": round(total / (statistics.median(times) / 1e3) / 1e9, 3),
+           "seg_per_strategy": {ahs.STRATEGY_NAMES[i]: int(info.seg_per_strategy[i]) for i in range(1, 6)}}
+    if per_array:
+        torch.cuda.synchronize()
+        e0.record()
+        for s in range(n_seg):
+            b, e = offs_l[s], offs_l[s + 1]
+            if e > b:
+                ctx.sort(keys[b:e], out=out[b:e], key_type=ahs.AHS_U32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["per_array_ms"] = round(ms, 3)
+        res["per_array_gkeys_s"] = round(total / (ms / 1e3) / 1e9, 3)
+        res["batched_over_per_array"] = round(ms / statistics.median(times), 2)
+    del keys, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5,
+               pool: int = 48, max_keys: int = 10**8):
+    """Poisson arrivals of uint32 sort requests (sizes log-uniform in
+    [10^3, max_keys], config-4 distributions, keys pre-generated on the device
+    into a pool of input buffers) at an offered load in Gkeys/s, through the
+    serving loop; and the same requests sorted serially one by one."""
+    import ctypes
+    import torch
+    import numpy as np
+    import paper_2506_20677_gb300 as ahs
+    from gen import device as gdev
+    from gen import host as gh
+    rng = np.random.default_rng(seed)
+    sizes = gh.log_uniform_lengths(pool, seed, 7, 1000, max_keys)
+    types = gh.below32(gh.draws(seed, 8, 0, pool), 4).astype(np.int64)
+    ins = []
+    for i in range(pool):
+        n = int(sizes[i])
+        t = int(types[i])
+        if t == 0:
+            ins.append(gdev.uniform_u32(n, seed, 100 + i, 4096))
+        elif t == 1:
+            ins.append(gdev.zipf_u32(n, seed, 200 + i, 300 + i))
+        elif t == 2:
+            ins.append(gdev.uniform_u32(n, seed, 400 + i, 1 << 32))
+        else:
+            ins.append(gdev.swaps_u32(gdev.sorted_u32(gdev.uniform_u32(n, seed, 500 + i, 1 << 32)),
+                                      n // 100, seed, 600 + i))
+    outs = [torch.empty_like(x) for x in ins]
+    torch.cuda.synchronize()
+    mean = float(np.mean(sizes))
+    rate = load_gkeys * 1e9 / mean                       # requests per second
+    ctx = ahs.Context(ctx_device)
+    cfg = ahs.ahs_serve_config_t(64 << 30, 256, 100)
+    ahs.check(ahs.lib.ahs_serve_start(ctx.handle, ctypes.byref(cfg)), "ahs_serve_start")
+    busy = [False] * pool
+    pending = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    submitted = skipped = 0
+    while True:
+        now = time.perf_counter()
+        if now - t_start >= seconds:
+            break
+        # reap finished requests so their buffers can be reused
+        still = []
+        for tk, i in pending:
+            r = ahs.ahs_result_t()
+            if ahs.lib.ahs_serve_poll(ctx.handle, tk, 0, ctypes.byref(r)) == ahs.AHS_OK:
+                busy[i] = False
+            else:
+                still.append((tk, i))
+        pending = still
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.0005))
+            continue
+        t_next += rng.exponential(1.0 / rate)
+        free = [i for i in range(pool) if not busy[i]]
+        if not free:
+            skipped += 1
+            continue
+        i = free[int(rng.integers(0, len(free)))]
+        req = ahs.ahs_request_t(ins[i].data_ptr(), outs[i].data_ptr(), ins[i].numel(), ahs.AHS_U32)
+        tk = ctypes.c_uint64()
+        ahs.check(ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(req), ctypes.byref(tk)), "submit")
+        busy[i] = True
+        pending.append((tk.value, i))
+        submitted += 1
+    for tk, i in pending:
+        r = ahs.ahs_result_t()
+        ahs.lib.ahs_serve_poll(ctx.handle, tk, 600000, ctypes.byref(r))
+    elapsed = time.perf_counter() - t_start
+    st = ahs.ahs_serve_stats_t()
+    ahs.check(ahs.lib.ahs_serve_stats(ctx.handle, ctypes.byref(st)), "stats")
+    ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "stop")
+    # serial per-request baseline: the same pool, one request at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(pool):
+        ctx.sort(ins[i], out=outs[i], key_type=ahs.AHS_U32)
+    torch.cuda.synchronize()
+    serial = float(np.sum(sizes)) / (time.perf_counter() - t0) / 1e9
+    ctx.close()
+    return {"offered_gkeys_s": load_gkeys, "seconds": round(elapsed, 2), "submitted": submitted,
+            "dropped_no_free_buffer": skipped, "completed": int(st.completed),
+            "sustained_gkeys_s": round(st.keys / elapsed / 1e9, 3),
+            "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
+            "batches": int(st.batches), "peak_reserved_gb": round(st.peak_reserved_bytes / 2**30, 2),
+            "serial_per_request_gkeys_s": round(serial, 3),
+            "sizes": "log-uniform [1e3, %d] keys, pool of %d pre-generated requests" % (max_keys, pool)}
 
 
 def run_case(args, local):
@@ -411,10 +562,30 @@ def main():
     p.add_argument("--case", choices=list(VARIANTS) + ["3"], default=None,
                    help="diagnostic: one array of config 2 (a-f) or config 3, see --force")
     p.add_argument("--force", choices=["auto", "counting", "radix", "general"], default="auto")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
+    p.add_argument("--batch-segments", type=int, default=10_000,
+                   help="segments of the config-4 batch in the default run")
+    p.add_argument("--serve-load", type=float, default=5.0, help="offered Gkeys/s (default run)")
+    p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--batch", action="store_true", help="config 4 at full size: batched vs per-array")
+    p.add_argument("--serve", action="store_true", help="config 5: offered loads 2/5/10 Gkeys/s")
     args = p.parse_args()
     world, rank, local = dist_setup()
     if args.case is not None:
         run_case(args, local)
+        return
+    if args.batch or args.serve:
+        import torch
+        torch.cuda.set_device(local)
+        import paper_2506_20677_gb300 as ahs
+        out = {}
+        if args.batch:
+            ctx = ahs.Context(local)
+            out["batched"] = run_batched(ctx, 100_000, args.steps)
+            ctx.close()
+        if args.serve:
+            out["served"] = [run_served(local, load, args.serve_seconds) for load in (2.0, 5.0, 10.0)]
+        print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

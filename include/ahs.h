@@ -108,13 +108,19 @@ typedef struct {
 } ahs_thresholds_t;
 
 typedef struct {
-    int32_t device;              /* CUDA device ordinal */
+    int32_t device;              /* CUDA device ordinal; -1: host-only context (selection only) */
     ahs_select_mode select_mode; /* used by ahs_sort / ahs_sort_batch with AHS_AUTO */
     ahs_thresholds_t thresholds; /* for AHS_SEL_CUSTOM */
     const char* model_path;      /* tree table for AHS_SEL_MODEL (NULL: none loaded) */
     uint64_t workspace_limit;    /* bytes of device workspace the ctx may hold, 0 = no limit */
     int32_t timing;              /* 1: record per-phase device times into info structs */
+    uint32_t debug_flags;        /* AHS_DEBUG_* test hooks, 0 in normal use */
 } ahs_config_t;
+
+/* Test hook: in every radix pass, tile 1 does not publish its counts, so the
+ * later tiles' bounded look-back waits run out (about a second) and the call
+ * returns AHS_ERR_DEVICE_TIMEOUT with the context still usable. */
+#define AHS_DEBUG_STALL_ONE_TILE 1u
 
 /* Filled by ahs_sort when non-NULL. */
 typedef struct {

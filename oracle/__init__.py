@@ -88,6 +88,12 @@ def open_library(path: str):
     L.orc_quicksort.argtypes = [vp, vp, u64, i32]
     L.orc_sort.argtypes = [vp, vp, vp, vp, u64, i32, i32, ctypes.POINTER(Fsm),
                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Features)]
+    L.orc_model_load.argtypes = [ctypes.c_char_p]
+    L.orc_model_load.restype = vp
+    L.orc_model_free.argtypes = [vp]
+    L.orc_model_predict.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.orc_select_model.argtypes = [ctypes.POINTER(Features), vp, ctypes.c_uint32, i32,
+                                   ctypes.POINTER(Fsm), u64]
     return L
 
 
@@ -216,3 +222,29 @@ def sort(keys, vals=None, force: int = AUTO, profile: Profile = PAPER):
     _check(lib().orc_sort(_ptr(keys), _ptr(out), _ptr(vals), _ptr(vo), len(keys), _key_type(keys),
                           force, ctypes.byref(p), ctypes.byref(chosen), ctypes.byref(f)), "sort")
     return out, vo, chosen.value, f
+
+
+class Model:
+    """A tree table loaded by the oracle's own evaluator."""
+
+    def __init__(self, path: str):
+        self.h = lib().orc_model_load(os.fsencode(path))
+        if not self.h:
+            raise RuntimeError(f"oracle could not load tree table {path}")
+
+    def predict(self, x) -> int:
+        arr = (ctypes.c_double * len(x))(*[float(v) for v in x])
+        return lib().orc_model_predict(self.h, arr)
+
+    def select(self, f: Features, key_bytes: int, payload: bool, rules: Profile,
+               small_capacity: int) -> int:
+        p = rules.c()
+        return lib().orc_select_model(ctypes.byref(f), self.h, key_bytes, int(payload),
+                                      ctypes.byref(p), small_capacity)
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().orc_model_free(self.h)
+        except Exception:
+            pass

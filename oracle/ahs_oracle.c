@@ -5,6 +5,7 @@
 #include "ahs_oracle.h"
 
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -371,6 +372,114 @@ int orc_merge_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* 
     store_all(out, a, n, t);
     free(a); free(ta); free(tv);
     return ORC_OK;
+}
+
+/* --------------------------------------- Section III-H: the learned selector */
+
+struct orc_model {
+    int n_classes, n_features, n_trees;
+    int* classes;
+    int* tree_start;     /* first node of each tree */
+    int* feature;        /* per node (-1: leaf) */
+    double* threshold;
+    int* left;
+    int* right;
+    double* value;       /* n_classes per node */
+};
+
+void orc_model_free(orc_model* m) {
+    if (!m) return;
+    free(m->classes); free(m->tree_start); free(m->feature); free(m->threshold);
+    free(m->left); free(m->right); free(m->value); free(m);
+}
+
+orc_model* orc_model_load(const char* path) {
+    FILE* fp = fopen(path, "r");
+    if (!fp) return NULL;
+    orc_model* m = (orc_model*)calloc(1, sizeof(orc_model));
+    char word[64];
+    int version = 0, ok = 1, cap = 1024, used = 0;
+    ok = m && fscanf(fp, "%63s %d", word, &version) == 2 && strcmp(word, "ahs-trees") == 0 && version == 1;
+    ok = ok && fscanf(fp, "%63s %d", word, &m->n_classes) == 2 && m->n_classes > 0 && m->n_classes <= 16;
+    if (ok) m->classes = (int*)malloc(sizeof(int) * m->n_classes);
+    for (int c = 0; ok && c < m->n_classes; ++c) ok = fscanf(fp, "%d", &m->classes[c]) == 1;
+    ok = ok && fscanf(fp, "%63s %d", word, &m->n_features) == 2 && m->n_features > 0;
+    ok = ok && fscanf(fp, "%63s %d", word, &m->n_trees) == 2 && m->n_trees > 0;
+    if (ok) {
+        m->tree_start = (int*)malloc(sizeof(int) * (m->n_trees + 1));
+        m->feature = (int*)malloc(sizeof(int) * cap);
+        m->threshold = (double*)malloc(sizeof(double) * cap);
+        m->left = (int*)malloc(sizeof(int) * cap);
+        m->right = (int*)malloc(sizeof(int) * cap);
+        m->value = (double*)malloc(sizeof(double) * cap * m->n_classes);
+    }
+    for (int t = 0; ok && t < m->n_trees; ++t) {
+        int nodes = 0;
+        ok = fscanf(fp, "%63s %d", word, &nodes) == 2 && nodes > 0;
+        m->tree_start[t] = used;
+        for (int i = 0; ok && i < nodes; ++i) {
+            if (used == cap) {
+                cap *= 2;
+                m->feature = (int*)realloc(m->feature, sizeof(int) * cap);
+                m->threshold = (double*)realloc(m->threshold, sizeof(double) * cap);
+                m->left = (int*)realloc(m->left, sizeof(int) * cap);
+                m->right = (int*)realloc(m->right, sizeof(int) * cap);
+                m->value = (double*)realloc(m->value, sizeof(double) * cap * m->n_classes);
+            }
+            ok = fscanf(fp, "%d %lf %d %d", &m->feature[used], &m->threshold[used], &m->left[used],
+                        &m->right[used]) == 4;
+            for (int c = 0; ok && c < m->n_classes; ++c)
+                ok = fscanf(fp, "%lf", &m->value[(size_t)used * m->n_classes + c]) == 1;
+            if (ok && m->feature[used] >= 0)      /* children are local indices of this tree */
+                ok = m->feature[used] < m->n_features && m->left[used] > i && m->left[used] < nodes &&
+                     m->right[used] > i && m->right[used] < nodes;
+            ++used;
+        }
+    }
+    if (ok) m->tree_start[m->n_trees] = used;
+    fclose(fp);
+    if (!ok) { orc_model_free(m); return NULL; }
+    return m;
+}
+
+int orc_model_predict(const orc_model* m, const double* x) {
+    double score[16] = {0};
+    for (int t = 0; t < m->n_trees; ++t) {
+        const int base = m->tree_start[t];
+        int i = 0;                                   /* local node index */
+        while (m->feature[base + i] >= 0) {
+            const float xf = (float)x[m->feature[base + i]];
+            i = ((double)xf <= m->threshold[base + i]) ? m->left[base + i] : m->right[base + i];
+        }
+        for (int c = 0; c < m->n_classes; ++c) score[c] += m->value[(size_t)(base + i) * m->n_classes + c];
+    }
+    int best = 0;
+    for (int c = 1; c < m->n_classes; ++c)
+        if (score[c] > score[best]) best = c;
+    return m->classes[best];
+}
+
+int orc_select_model(const orc_features_t* f, const orc_model* m, uint32_t key_bytes, int payload,
+                     const orc_fsm_t* rules, uint64_t small_capacity) {
+    int s;
+    if (f->n < 1000 || !m) {
+        s = orc_select(f, rules);
+    } else if (f->n <= 1 || f->span == 0 || (rules->sorted_identity && f->descents == 0)) {
+        s = ORC_IDENTITY;
+    } else {
+        double x[5];
+        x[0] = log2((double)f->n);
+        x[1] = log2((double)f->span + 1.0);
+        x[2] = f->entropy_norm;
+        x[3] = (double)key_bytes;
+        x[4] = payload ? 1.0 : 0.0;
+        s = orc_model_predict(m, x);
+        if (s == ORC_COUNTING && f->span > 65535) s = ORC_GENERAL;
+        if (s == ORC_SMALL && f->n > rules->n_t) s = ORC_GENERAL;
+        if (s < ORC_IDENTITY || s > ORC_GENERAL) s = ORC_GENERAL;
+    }
+    if (s == ORC_SMALL && f->n > small_capacity) s = ORC_GENERAL;
+    return s;
 }
 
 /* -------------------------------------------------------- the whole pipeline */

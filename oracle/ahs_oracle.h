@@ -76,6 +76,21 @@ int orc_quicksort(const void* keys, void* out, uint64_t n, int key_type);
 int orc_merge_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
                    uint64_t n, int key_type);
 
+/* Learned selector (Section III-H): a tree table (see the format in
+ * paper_2506_20677_gb300/selector/train_trees.py) evaluated on
+ * x = (log2 n, log2 k, h, key bytes, has payload).  An inner node goes left
+ * when float32(x[f]) <= threshold; the class with the largest summed leaf
+ * score wins, the first on ties. */
+typedef struct orc_model orc_model;
+orc_model* orc_model_load(const char* path);
+void orc_model_free(orc_model* m);
+int orc_model_predict(const orc_model* m, const double* x);
+/* Table IV: static rules (the thresholds in `rules`) below n = 1000, the model
+ * above; counting only for k <= 2^16 and the one-block sort only up to
+ * n_t and small_capacity, otherwise the general path. */
+int orc_select_model(const orc_features_t* f, const orc_model* m, uint32_t key_bytes, int payload,
+                     const orc_fsm_t* rules, uint64_t small_capacity);
+
 /* Features -> select (unless forced) -> run.  *chosen receives the strategy run. */
 int orc_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
              uint64_t n, int key_type, int force, const orc_fsm_t* fsm,

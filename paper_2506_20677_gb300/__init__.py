@@ -25,6 +25,7 @@ AHS_OK, AHS_ERR_INVALID_ARG, AHS_ERR_DTYPE, AHS_ERR_OOM, AHS_ERR_BUDGET, AHS_ERR
 AHS_U32, AHS_U64, AHS_I32, AHS_I64 = range(4)
 AHS_AUTO, AHS_IDENTITY, AHS_SMALL, AHS_COUNTING, AHS_RADIX, AHS_GENERAL = range(6)
 AHS_SEL_PAPER, AHS_SEL_LISTING6, AHS_SEL_GB300, AHS_SEL_MODEL, AHS_SEL_CUSTOM = range(5)
+AHS_DEBUG_STALL_ONE_TILE = 1
 STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL")
 
 
@@ -45,7 +46,8 @@ class ahs_thresholds_t(ctypes.Structure):
 class ahs_config_t(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("select_mode", ctypes.c_int),
                 ("thresholds", ahs_thresholds_t), ("model_path", ctypes.c_char_p),
-                ("workspace_limit", ctypes.c_uint64), ("timing", ctypes.c_int32)]
+                ("workspace_limit", ctypes.c_uint64), ("timing", ctypes.c_int32),
+                ("debug_flags", ctypes.c_uint32)]
 
 
 class ahs_sort_info_t(ctypes.Structure):
@@ -186,13 +188,15 @@ class Context:
     """An ahs_ctx on one device (owns the device workspace)."""
 
     def __init__(self, device: int = 0, select_mode: int = AHS_SEL_GB300, model_path=None,
-                 timing: bool = False, workspace_limit: int = 0, thresholds=None):
+                 timing: bool = False, workspace_limit: int = 0, thresholds=None,
+                 debug_flags: int = 0):
         cfg = ahs_config_t()
         lib.ahs_default_config(ctypes.byref(cfg))
         cfg.device = device
         cfg.select_mode = select_mode
         cfg.timing = int(timing)
         cfg.workspace_limit = workspace_limit
+        cfg.debug_flags = debug_flags
         self._model_path = None if model_path is None else os.fsencode(model_path)
         cfg.model_path = self._model_path
         if thresholds is not None:

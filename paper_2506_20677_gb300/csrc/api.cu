@@ -218,7 +218,8 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
         RadixScratch rs = radix_carve(static_cast<char*>(ctx->ws) + freg, n, kd.bytes,
                                       vin != nullptr, plan.passes);
         e = launch_radix_sort(kin, kout, vin, vout, n, kd, min_ord, plan, rs, ctx->d_rec,
-                              ctx->d_err, ctx->sms, st);
+                              ctx->d_err, ctx->sms, st,
+                              (ctx->cfg.debug_flags & AHS_DEBUG_STALL_ONE_TILE) ? 1u : ~0u);
         *passes = plan.passes;
         return cuda_status(ctx, e);
     }
@@ -284,6 +285,18 @@ ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg) {
     }
     ctx->custom = ctx->cfg.thresholds;
     ctx->device = ctx->cfg.device;
+    if (ctx->device < 0) {
+        // Host-only context: selection and model loading, no device work.
+        if (ctx->cfg.model_path) {
+            std::string why;
+            if (!ctx->model.load(ctx->cfg.model_path, &why)) {
+                delete ctx;
+                return AHS_ERR_NOT_FOUND;
+            }
+        }
+        *out = ctx;
+        return AHS_OK;
+    }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const size_t persist = 256 + 256;
@@ -320,6 +333,10 @@ ahs_status ahs_serve_stop(ahs_ctx* ctx);
 
 void ahs_destroy(ahs_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->device < 0) {
+        delete ctx;
+        return;
+    }
     if (ctx->serve) ahs_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
@@ -381,7 +398,7 @@ static bool valid_type(ahs_key_type t) { return t >= AHS_U32 && t <= AHS_I64; }
 
 ahs_status ahs_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_type type,
                         void* stream, ahs_features_t* h_out) {
-    if (!ctx || !h_out) return AHS_ERR_INVALID_ARG;
+    if (!ctx || !h_out || ctx->device < 0) return AHS_ERR_INVALID_ARG;
     if (!valid_type(type)) return AHS_ERR_DTYPE;
     if (n && !d_keys) return AHS_ERR_INVALID_ARG;
     if (n == 0) {
@@ -427,7 +444,7 @@ ahs_status ahs_sort(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
                     const uint32_t* d_vals_in, uint32_t* d_vals_out, uint64_t n,
                     ahs_key_type type, ahs_strategy force, void* stream, ahs_sort_info_t* info) {
     if (info) std::memset(info, 0, sizeof(*info));
-    if (!ctx) return AHS_ERR_INVALID_ARG;
+    if (!ctx || ctx->device < 0) return AHS_ERR_INVALID_ARG;
     if (!valid_type(type)) return AHS_ERR_DTYPE;
     if (force < AHS_AUTO || force > AHS_GENERAL) return AHS_ERR_INVALID_ARG;
     if (n && (!d_keys_in || !d_keys_out)) return AHS_ERR_INVALID_ARG;

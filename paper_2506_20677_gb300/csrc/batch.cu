@@ -437,7 +437,7 @@ extern "C" ahs_status ahs_sort_batch(ahs_ctx* ctx, const void* d_keys_in, void* 
                                      const uint64_t* h_seg_offsets, uint32_t n_seg,
                                      ahs_key_type type, void* stream, ahs_batch_info_t* info) {
     if (info) std::memset(info, 0, sizeof(*info));
-    if (!ctx || (n_seg && !h_seg_offsets)) return AHS_ERR_INVALID_ARG;
+    if (!ctx || ctx->device < 0 || (n_seg && !h_seg_offsets)) return AHS_ERR_INVALID_ARG;
     if (type < AHS_U32 || type > AHS_I64) return AHS_ERR_DTYPE;
     if (n_seg == 0) return AHS_OK;
     for (uint32_t s = 0; s < n_seg; ++s) {

@@ -69,7 +69,7 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
                                          (int)sizeof(Smem));
     if (e != cudaSuccess) return e;
     // Grids are limited to 2^31 - 1 blocks in x; bucket lists are far smaller.
-    TraceScope ts(T == 128 ? "bucket_sort_1k" : (T == 256 ? "bucket_sort_4k" : "bucket_sort_8k"), keys, st);
+    TraceScope ts(T * IPT <= 1024 ? "bucket_sort_1k" : (T * IPT <= 2048 ? "bucket_sort_2k" : (T * IPT <= 4096 ? "bucket_sort_4k" : "bucket_sort_8k")), keys, st);
     fn<<<count, T, sizeof(Smem), st>>>(d_list, static_cast<const K*>(b0), static_cast<const K*>(b1),
                                        static_cast<const K*>(b2), static_cast<K*>(out), vb0, vb1,
                                        vb2, vout, flip);
@@ -77,17 +77,20 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
 }
 
 template <typename K, bool VALS>
-cudaError_t finish_t(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                     const uint64_t keys[3], const void* b0, const void* b1, const void* b2,
+cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t counts[kBucketClasses],
+                     const uint64_t keys[kBucketClasses], const void* b0, const void* b1, const void* b2,
                      void* out, const uint32_t* vb0, const uint32_t* vb1, const uint32_t* vb2,
                      uint32_t* vout, K flip, cudaStream_t st) {
     cudaError_t e = finish_class<K, VALS, 128, 8>(d_lists[0], counts[0], keys[0], b0, b1, b2, out,
                                                   vb0, vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 256, 16>(d_lists[1], counts[1], keys[1], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 256, 8>(d_lists[1], counts[1], keys[1], b0, b1, b2, out, vb0,
+                                          vb1, vb2, vout, flip, st);
+    if (e == cudaSuccess)
+        e = finish_class<K, VALS, 256, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 512, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 512, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     return e;
 }
@@ -97,9 +100,9 @@ cudaError_t finish_t(const FinalBucket* d_lists[3], const uint32_t counts[3],
 uint64_t blocksort_capacity(uint32_t, bool) { return kBucketCap; }
 
 uint32_t bucket_class(uint32_t size) {
-    if (size <= kBucketClassCap[0]) return 0;
-    if (size <= kBucketClassCap[1]) return 1;
-    return 2;
+    for (int c = 0; c < kBucketClasses - 1; ++c)
+        if (size <= kBucketClassCap[c]) return c;
+    return kBucketClasses - 1;
 }
 
 cudaError_t launch_blocksort_single(const void* keys_in, void* keys_out, const uint32_t* vals_in,
@@ -120,8 +123,9 @@ cudaError_t launch_blocksort_single(const void* keys_in, void* keys_out, const u
              : single_t<uint64_t, false, 512, 16>(keys_in, keys_out, nullptr, nullptr, m, kd.flip, st);
 }
 
-cudaError_t launch_bucket_finish(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                                 const uint64_t keys[3], const void* buf0, const void* buf1,
+cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
+                                 const uint32_t counts[kBucketClasses],
+                                 const uint64_t keys[kBucketClasses], const void* buf0, const void* buf1,
                                  const void* buf2, void* out, const uint32_t* vbuf0,
                                  const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
                                  KeyDesc kd, cudaStream_t st) {

@@ -7,6 +7,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "rank.cuh"
 
 namespace ahs {
 
@@ -17,6 +18,7 @@ struct BlockSortSmem {
     static constexpr int W = THREADS / 32;
     static constexpr int CAP = THREADS * IPT;
     uint32_t warp_hist[W][kBsRadix];
+    uint32_t warp_mask[kRankBlockSort == kRankAtomicOr ? W : 1][kBsRadix];
     uint32_t tile_count[kBsRadix];
     uint32_t tile_start[kBsRadix];
     uint32_t scan[W + 1];
@@ -72,24 +74,24 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
     }
     const uint32_t D = m ? bitlen64((unsigned long long)(K)(hi - lo)) : 0;
     const uint32_t passes = (D + 7) / 8;
-    const uint32_t lt = lanemask_lt();
 
+    if constexpr (kRankBlockSort == kRankAtomicOr) {
+        for (uint32_t i = tid; i < W * kBsRadix; i += THREADS) (&S.warp_mask[0][0])[i] = 0;
+    }
     for (uint32_t pass = 0; pass < passes; ++pass) {
         const uint32_t shift = 8 * pass;
         for (uint32_t i = tid; i < W * kBsRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
         __syncthreads();
-        uint32_t dig[IPT], rank[IPT];
-        uint32_t* wh = S.warp_hist[warp];
+        uint32_t dr[IPT];
+        {
+            uint32_t dig[IPT];
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const uint32_t p = wbase + 32 * i + lane;
-            dig[i] = p < m ? (uint32_t)(((K)(key[i] ^ flip) - lo) >> shift) & 0xffu : (uint32_t)kBsRadix;
-            const uint32_t peers = __match_any_sync(AHS_FULL_MASK, dig[i]);
-            const uint32_t leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (lane == leader && dig[i] < (uint32_t)kBsRadix) old = atomicAdd(&wh[dig[i]], __popc(peers));
-            old = __shfl_sync(AHS_FULL_MASK, old, leader);
-            rank[i] = old + __popc(peers & lt);
+            for (int i = 0; i < IPT; ++i) {
+                const uint32_t p = wbase + 32 * i + lane;
+                dig[i] = p < m ? (uint32_t)(((K)(key[i] ^ flip) - lo) >> shift) & 0xffu : (uint32_t)kBsRadix;
+            }
+            warp_rank<IPT, kBsRadix, kRankBlockSort>(dig, dr, S.warp_hist[warp],
+                                                S.warp_mask[kRankBlockSort == kRankAtomicOr ? warp : 0]);
         }
         __syncthreads();
         for (uint32_t d = tid; d < (uint32_t)kBsRadix; d += THREADS) {
@@ -104,10 +106,12 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
         }
         __syncthreads();
         scan_digit_counts<THREADS, kBsRadix>(S.tile_count, S.tile_start, S.scan);
+        constexpr int SH = RankPack<kBsRadix>::kShift;
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            if (dig[i] < (uint32_t)kBsRadix) {
-                const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
+            const uint32_t d = dr[i] & RankPack<kBsRadix>::kMask;
+            if (d < (uint32_t)kBsRadix) {
+                const uint32_t lp = S.tile_start[d] + S.warp_hist[warp][d] + (dr[i] >> SH);
                 if (AHS_DCHECK(lp < m, "blocksort stage", lp)) {
                     S.keys[lp] = key[i];
                     if constexpr (VALS) S.vals[lp] = val[i];

@@ -90,10 +90,11 @@ struct RadixScratch {
 };
 RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes);
 // Stable LSD radix sort over ord(x) - min (onesweep passes with decoupled look-back).
+// stall_tile: a tile that withholds its look-back publication (test hook), or ~0u.
 cudaError_t launch_radix_sort(const void* keys_in, void* keys_out, const uint32_t* vals_in,
                               uint32_t* vals_out, uint64_t n, KeyDesc kd, uint64_t min_ord,
                               const RadixPlan& plan, const RadixScratch& rs, DevFeatures* rec,
-                              uint32_t* err, int sms, cudaStream_t st);
+                              uint32_t* err, int sms, cudaStream_t st, uint32_t stall_tile = ~0u);
 
 // ------------------------------------------------------- one-block sort (SMALL)
 uint64_t blocksort_capacity(uint32_t key_bytes, bool has_vals);

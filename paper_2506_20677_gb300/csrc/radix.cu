@@ -12,6 +12,7 @@
 // reads the keys once before the first pass.
 #include "common.cuh"
 #include "internal.h"
+#include "rank.cuh"
 #include "trace.h"
 
 namespace ahs {
@@ -102,6 +103,7 @@ struct OnesweepSmem {
     static constexpr int W = THREADS / 32;
     static constexpr int TILE = THREADS * IPT;
     uint32_t warp_hist[W][kRadix];
+    uint32_t warp_mask[kRankOnesweep == kRankAtomicOr ? W : 1][kRadix];
     uint32_t tile_count[kRadix];
     uint32_t tile_start[kRadix];
     uint32_t gbase[kRadix];
@@ -111,14 +113,15 @@ struct OnesweepSmem {
     uint32_t vals[VALS ? TILE : 1];
 };
 
-template <typename K, bool VALS, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS)
+template <typename K, bool VALS, int THREADS, int IPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
               const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ vals_out, uint32_t n,
               K mn, K flip, uint32_t shift, uint32_t bits, const uint32_t* __restrict__ dbase,
               uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
-              uint32_t* __restrict__ err) {
+              uint32_t* __restrict__ err, uint32_t stall_tile) {
     using Smem = OnesweepSmem<K, VALS, THREADS, IPT>;
+    static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
     constexpr int W = Smem::W;
     constexpr int TILE = Smem::TILE;
     constexpr int WARP_ITEMS = 32 * IPT;
@@ -130,6 +133,8 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
 
     if (tid == 0) S.tile_id = atomicAdd(tile_counter, 1u);
     for (uint32_t i = tid; i < W * kRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
+    if constexpr (kRankOnesweep == kRankAtomicOr)
+        for (uint32_t i = tid; i < W * kRadix; i += THREADS) (&S.warp_mask[0][0])[i] = 0;
     __syncthreads();
     const uint32_t tile = S.tile_id;
     if (!AHS_DCHECK(tile < gridDim.x, "onesweep tile id", tile)) return;
@@ -153,17 +158,8 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
 
     // Rank within the warp in input order (stable): peers share a digit.
     uint32_t rank[IPT];
-    uint32_t* wh = S.warp_hist[warp];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const uint32_t peers = __match_any_sync(AHS_FULL_MASK, dig[i]);
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && dig[i] < kRadix) old = atomicAdd(&wh[dig[i]], __popc(peers));
-        old = __shfl_sync(AHS_FULL_MASK, old, leader);
-        rank[i] = old + __popc(peers & lt);
-    }
+    warp_rank<IPT, kRadix, kRankOnesweep, false>(dig, rank, S.warp_hist[warp],
+                                                 S.warp_mask[kRankOnesweep == kRankAtomicOr ? warp : 0]);
     __syncthreads();
 
     // Per digit: exclusive prefix over warps and the tile's count.
@@ -177,7 +173,8 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
         }
         S.tile_count[d] = run;
         // Publish this tile's aggregate as early as possible.
-        st_relaxed_gpu(&status[(size_t)tile * kRadix + d], (tile == 0 ? kFlagIncl : kFlagAgg) | run);
+        if (tile != stall_tile)
+            st_relaxed_gpu(&status[(size_t)tile * kRadix + d], (tile == 0 ? kFlagIncl : kFlagAgg) | run);
     }
     __syncthreads();
     scan_digit_counts<THREADS, kRadix>(S.tile_count, S.tile_start, S.scan);
@@ -185,7 +182,7 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
     // Stage the tile in digit order.
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        if (dig[i] < kRadix) {
+        if (dig[i] < (uint32_t)kRadix) {
             const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
             if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep stage", lp)) S.keys[lp] = key[i];
         }
@@ -193,17 +190,16 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
     if constexpr (VALS) {
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            const uint32_t idx = wbase + 32 * i + lane;
-            if (dig[i] < kRadix) {
+            if (dig[i] < (uint32_t)kRadix) {
                 const uint32_t lp = S.tile_start[dig[i]] + S.warp_hist[warp][dig[i]] + rank[i];
-                if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep vstage", lp)) S.vals[lp] = vals_in[idx];
+                if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep vstage", lp))
+                    S.vals[lp] = vals_in[wbase + 32 * i + lane];
             }
         }
     }
 
-    // Decoupled look-back: exclusive prefix of this digit over earlier tiles.
-    if (tid < (uint32_t)kRadix) {
-        const uint32_t d = tid;
+    // Decoupled look-back: exclusive prefix of each digit over earlier tiles.
+    for (uint32_t d = tid; d < (uint32_t)kRadix; d += THREADS) {
         uint32_t excl = 0;
         if (tile > 0) {
             int64_t j = (int64_t)tile - 1;
@@ -222,7 +218,8 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
                 if (flag == kFlagIncl) break;
                 --j;
             }
-            st_relaxed_gpu(&status[(size_t)tile * kRadix + d], kFlagIncl | (excl + S.tile_count[d]));
+            if (tile != stall_tile)
+                st_relaxed_gpu(&status[(size_t)tile * kRadix + d], kFlagIncl | (excl + S.tile_count[d]));
         }
         S.gbase[d] = dbase[d] + excl - S.tile_start[d];
     }
@@ -240,12 +237,13 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
     }
 }
 
+// Tile shapes (threads x keys per thread, minimum resident CTAs per SM).
 template <typename K, bool VALS>
 struct OnesweepCfg;
-template <> struct OnesweepCfg<uint32_t, false> { static constexpr int T = 512, IPT = 16; };
-template <> struct OnesweepCfg<uint32_t, true> { static constexpr int T = 512, IPT = 12; };
-template <> struct OnesweepCfg<uint64_t, false> { static constexpr int T = 512, IPT = 12; };
-template <> struct OnesweepCfg<uint64_t, true> { static constexpr int T = 512, IPT = 8; };
+template <> struct OnesweepCfg<uint32_t, false> { static constexpr int T = 512, IPT = 16, MINB = 2; };
+template <> struct OnesweepCfg<uint32_t, true> { static constexpr int T = 512, IPT = 12, MINB = 2; };
+template <> struct OnesweepCfg<uint64_t, false> { static constexpr int T = 512, IPT = 12, MINB = 2; };
+template <> struct OnesweepCfg<uint64_t, true> { static constexpr int T = 512, IPT = 8, MINB = 2; };
 
 template <typename K, bool VALS>
 constexpr int tile_keys() { return OnesweepCfg<K, VALS>::T * OnesweepCfg<K, VALS>::IPT; }
@@ -253,8 +251,9 @@ constexpr int tile_keys() { return OnesweepCfg<K, VALS>::T * OnesweepCfg<K, VALS
 template <typename K, bool VALS>
 cudaError_t radix_t(const void* kin_v, void* kout_v, const uint32_t* vin, uint32_t* vout,
                     uint64_t n, K flip, K mn, const RadixPlan& plan, const RadixScratch& rs,
-                    DevFeatures* rec, uint32_t* err, int sms, cudaStream_t st) {
-    constexpr int T = OnesweepCfg<K, VALS>::T, IPT = OnesweepCfg<K, VALS>::IPT;
+                    DevFeatures* rec, uint32_t* err, int sms, cudaStream_t st, uint32_t stall_tile) {
+    constexpr int T = OnesweepCfg<K, VALS>::T, IPT = OnesweepCfg<K, VALS>::IPT,
+                  MINB = OnesweepCfg<K, VALS>::MINB;
     constexpr int TILE = T * IPT;
     using Smem = OnesweepSmem<K, VALS, T, IPT>;
     const K* kin = static_cast<const K*>(kin_v);
@@ -290,7 +289,7 @@ cudaError_t radix_t(const void* kin_v, void* kout_v, const uint32_t* vin, uint32
 
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(onesweep_pass<K, VALS, T, IPT>,
+        e = cudaFuncSetAttribute(onesweep_pass<K, VALS, T, IPT, MINB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e != cudaSuccess) return e;
         attr = true;
@@ -317,9 +316,9 @@ cudaError_t radix_t(const void* kin_v, void* kout_v, const uint32_t* vin, uint32
         uint32_t* vdst = to_out ? vout : rs.vals_tmp;
         uint32_t* status = rs.status + (size_t)p * tiles * kRadix;
         TraceScope ts("radix_onesweep", n, st);
-        onesweep_pass<K, VALS, T, IPT><<<(uint32_t)tiles, T, sizeof(Smem), st>>>(
+        onesweep_pass<K, VALS, T, IPT, MINB><<<(uint32_t)tiles, T, sizeof(Smem), st>>>(
             src, dst, vsrc, vdst, (uint32_t)n, mn, flip, plan.shift[p], plan.bits[p],
-            dbase + p * kRadix, status, rs.tile_counters + p, err);
+            dbase + p * kRadix, status, rs.tile_counters + p, err, stall_tile);
         src = dst;
         vsrc = vdst;
     }
@@ -375,19 +374,19 @@ RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_va
 cudaError_t launch_radix_sort(const void* keys_in, void* keys_out, const uint32_t* vals_in,
                               uint32_t* vals_out, uint64_t n, KeyDesc kd, uint64_t min_ord,
                               const RadixPlan& plan, const RadixScratch& rs, DevFeatures* rec,
-                              uint32_t* err, int sms, cudaStream_t st) {
+                              uint32_t* err, int sms, cudaStream_t st, uint32_t stall_tile) {
     const bool v = vals_in != nullptr;
     if (kd.bytes == 4) {
         if (v) return radix_t<uint32_t, true>(keys_in, keys_out, vals_in, vals_out, n,
                                               (uint32_t)kd.flip, (uint32_t)min_ord, plan, rs, rec,
-                                              err, sms, st);
+                                              err, sms, st, stall_tile);
         return radix_t<uint32_t, false>(keys_in, keys_out, nullptr, nullptr, n, (uint32_t)kd.flip,
-                                        (uint32_t)min_ord, plan, rs, rec, err, sms, st);
+                                        (uint32_t)min_ord, plan, rs, rec, err, sms, st, stall_tile);
     }
     if (v) return radix_t<uint64_t, true>(keys_in, keys_out, vals_in, vals_out, n, kd.flip,
-                                          min_ord, plan, rs, rec, err, sms, st);
+                                          min_ord, plan, rs, rec, err, sms, st, stall_tile);
     return radix_t<uint64_t, false>(keys_in, keys_out, nullptr, nullptr, n, kd.flip, min_ord, plan,
-                                    rs, rec, err, sms, st);
+                                    rs, rec, err, sms, st, stall_tile);
 }
 
 }  // namespace ahs

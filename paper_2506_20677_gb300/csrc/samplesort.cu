@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "internal.h"
+#include "rank.cuh"
 #include "samplesort.h"
 #include "segsort.h"
 #include "trace.h"
@@ -44,6 +45,9 @@ constexpr uint32_t kMaxLevels = 16;
 constexpr int kSplit = 0;                       // bucket = splitter interval / equality
 constexpr int kDigit = 1;                       // bucket = 8-bit digit of key - segment min
 constexpr int kHistCopies = 4;
+static_assert(kThreads % 32 == 0 && kThreads >= 32, "whole warps");
+static_assert((uint32_t)kThreads * kIpt >= kSamples, "one CTA must hold the whole splitter sample");
+static_assert(kCols % kThreads == 0 || kThreads % kCols == 0, "bucket columns divide the block");
 
 struct SegDesc {
     unsigned long long begin;
@@ -237,6 +241,7 @@ template <typename K, bool VALS>
 struct ScatterSmem {
     K sp[2 * kSlots];
     uint32_t warp_hist[kThreads / 32][kCols];
+    uint32_t warp_mask[kRankScatter == kRankAtomicOr ? kThreads / 32 : 1][kCols];
     uint32_t tile_count[kCols];
     uint32_t tile_start[kCols];
     uint32_t gbase[kCols];
@@ -274,10 +279,12 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
         cls.shift = shift;
     }
     for (uint32_t i = tid; i < W * kCols; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
+    if constexpr (kRankScatter == kRankAtomicOr)
+        for (uint32_t i = tid; i < W * kCols; i += kThreads) (&S.warp_mask[0][0])[i] = 0;
     __syncthreads();
 
     K key[kIpt];
-    uint32_t b[kIpt], rank[kIpt];
+    uint32_t b[kIpt];
     const K* p = src + t.begin;
     const uint32_t wbase = warp * WARP_ITEMS;
 #pragma unroll
@@ -291,17 +298,9 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
             b[i] = kCols;
         }
     }
-    uint32_t* wh = S.warp_hist[warp];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < kIpt; ++i) {
-        const uint32_t peers = __match_any_sync(AHS_FULL_MASK, b[i]);
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (lane == leader && b[i] < kCols) old = atomicAdd(&wh[b[i]], __popc(peers));
-        old = __shfl_sync(AHS_FULL_MASK, old, leader);
-        rank[i] = old + __popc(peers & lt);
-    }
+    uint32_t dr[kIpt];
+    warp_rank<kIpt, kCols, kRankScatter>(b, dr, S.warp_hist[warp],
+                                      S.warp_mask[kRankScatter == kRankAtomicOr ? warp : 0]);
     __syncthreads();
     for (uint32_t j = tid; j < kCols; j += kThreads) {
         uint32_t run = 0;
@@ -318,23 +317,17 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
     for (uint32_t j = tid; j < kCols; j += kThreads)
         S.gbase[j] = (uint32_t)(offs[(size_t)blockIdx.x * kCols + j]) - S.tile_start[j];
     __syncthreads();
+    constexpr int SH = RankPack<kCols>::kShift;
+    const uint32_t* vp = VALS ? vsrc + t.begin : nullptr;
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) {
-        if (b[i] < kCols) {
-            const uint32_t lp = S.tile_start[b[i]] + S.warp_hist[warp][b[i]] + rank[i];
+        const uint32_t bk = dr[i] & RankPack<kCols>::kMask;
+        if (bk < kCols) {
+            const uint32_t lp = S.tile_start[bk] + S.warp_hist[warp][bk] + (dr[i] >> SH);
             if (!AHS_DCHECK(lp < t.size, "scatter stage", lp)) continue;
             S.keys[lp] = key[i];
-            S.bid[lp] = (uint16_t)b[i];
-        }
-    }
-    if constexpr (VALS) {
-        const uint32_t* vp = vsrc + t.begin;
-#pragma unroll
-        for (int i = 0; i < kIpt; ++i) {
-            if (b[i] < kCols) {
-                const uint32_t lp = S.tile_start[b[i]] + S.warp_hist[warp][b[i]] + rank[i];
-                if (AHS_DCHECK(lp < t.size, "scatter vstage", lp)) S.vals[lp] = vp[wbase + 32 * i + lane];
-            }
+            S.bid[lp] = (uint16_t)bk;
+            if constexpr (VALS) S.vals[lp] = vp[wbase + 32 * i + lane];
         }
     }
     __syncthreads();
@@ -475,7 +468,7 @@ cudaError_t set_attrs() {
 ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, const void* ktmp,
                           const void* kout, const void* kin, const uint32_t* vtmp, uint32_t* vout,
                           const uint32_t* vin, KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
-    std::vector<FinalBucket> cls[3];
+    std::vector<FinalBucket> cls[kBucketClasses];
     uint32_t nsorted = 0;
     for (const FinalBucket& f : finals) {
         cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
@@ -489,11 +482,11 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
     if (rc != AHS_OK) return rc;
     FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
     FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
-    const FinalBucket* lists[3];
-    uint32_t counts[3];
-    uint64_t keys[3];
+    const FinalBucket* lists[kBucketClasses];
+    uint32_t counts[kBucketClasses];
+    uint64_t keys[kBucketClasses];
     size_t at = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kBucketClasses; ++k) {
         std::memcpy(hf + at, cls[k].data(), cls[k].size() * sizeof(FinalBucket));
         lists[k] = df + at;
         counts[k] = (uint32_t)cls[k].size();

@@ -9,9 +9,10 @@
 namespace ahs {
 
 // Largest bucket one CTA sorts in shared memory, and the size classes of the
-// bucket kernels (128x8, 256x16 and 512x16 threads x keys).
+// bucket kernels (128x8, 256x8, 256x16 and 512x16 threads x keys).
 constexpr uint32_t kBucketCap = 8192;
-constexpr uint32_t kBucketClassCap[3] = {1024, 4096, 8192};
+constexpr int kBucketClasses = 4;
+constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 4096, 8192};
 
 // A bucket that leaves the partition levels: its keys sit in buffer `where`
 // (0: temporary, 1: the output, 2: the input) at [begin, begin + size).
@@ -25,8 +26,9 @@ struct FinalBucket {
 static_assert(sizeof(FinalBucket) == 16, "FinalBucket layout");
 
 uint32_t bucket_class(uint32_t size);
-cudaError_t launch_bucket_finish(const FinalBucket* d_lists[3], const uint32_t counts[3],
-                                 const uint64_t keys[3], const void* buf0, const void* buf1,
+cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
+                                 const uint32_t counts[kBucketClasses],
+                                 const uint64_t keys[kBucketClasses], const void* buf0, const void* buf1,
                                  const void* buf2, void* out, const uint32_t* vbuf0,
                                  const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
                                  KeyDesc kd, cudaStream_t st);

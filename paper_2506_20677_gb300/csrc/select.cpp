@@ -66,7 +66,8 @@ ahs_strategy select_fsm(const ahs_features_t& f, const ahs_thresholds_t& p) {
 //   then per tree:  nodes M  followed by M lines
 //      feature threshold left right v_0 .. v_{C-1}
 //   feature = -1 marks a leaf (its v_c are the class scores added);
-//   internal nodes go left when x[feature] < threshold.
+//   internal nodes go left when float32(x[feature]) <= threshold (the rule of
+//   the scikit-learn trees the table is written from).
 // The predicted class is the argmax of the summed leaf scores (first max wins).
 
 bool TreeModel::load(const char* path, std::string* why) {
@@ -111,7 +112,10 @@ int TreeModel::predict(const double* x) const {
     std::vector<double> score(C, 0.0);
     for (const auto& tree : trees_) {
         int m = 0;
-        while (tree[m].feature >= 0) m = x[tree[m].feature] < tree[m].threshold ? tree[m].left : tree[m].right;
+        while (tree[m].feature >= 0) {
+            const double xv = (double)(float)x[tree[m].feature];
+            m = xv <= tree[m].threshold ? tree[m].left : tree[m].right;
+        }
         for (int c = 0; c < C; ++c) score[c] += tree[m].value[c];
     }
     int best = 0;

@@ -214,7 +214,8 @@ using ahs::ServeState;
 extern "C" {
 
 ahs_status ahs_serve_start(ahs_ctx* ctx, const ahs_serve_config_t* cfg) {
-    if (!ctx || !cfg || cfg->budget_bytes == 0 || cfg->max_inflight == 0) return AHS_ERR_INVALID_ARG;
+    if (!ctx || ctx->device < 0 || !cfg || cfg->budget_bytes == 0 || cfg->max_inflight == 0)
+        return AHS_ERR_INVALID_ARG;
     if (ctx->serve) return AHS_ERR_INVALID_ARG;
     auto* s = new (std::nothrow) ServeState();
     if (!s) return AHS_ERR_OOM;
