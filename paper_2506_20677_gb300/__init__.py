@@ -184,6 +184,11 @@ class SortResult:
         return STRATEGY_NAMES[self.strategy]
 
 
+# Tree table trained on GB300 timing labels (selector/labels_gb300.json);
+# the default for AHS_SEL_MODEL contexts.
+SHIPPED_TREES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector", "ahs_trees.txt")
+
+
 class Context:
     """An ahs_ctx on one device (owns the device workspace)."""
 
@@ -197,6 +202,8 @@ class Context:
         cfg.timing = int(timing)
         cfg.workspace_limit = workspace_limit
         cfg.debug_flags = debug_flags
+        if model_path is None and select_mode == AHS_SEL_MODEL:
+            model_path = SHIPPED_TREES
         self._model_path = None if model_path is None else os.fsencode(model_path)
         cfg.model_path = self._model_path
         if thresholds is not None:

@@ -115,3 +115,16 @@ def test_host_only_context_refuses_device_work():
     assert ahs.lib.ahs_sort(h, ctypes.c_void_p(1), ctypes.c_void_p(1), None, None, 4, ahs.AHS_U32,
                             0, None, None) == ahs.AHS_ERR_INVALID_ARG
     ahs.lib.ahs_destroy(h)
+
+
+@pytest.mark.skipif(not os.path.exists(SHIPPED), reason="no trained table shipped yet")
+def test_shipped_table_matches_its_labels(orc):
+    """The shipped table, evaluated by the oracle, reproduces most of the GB300
+    timing labels it was trained on (n >= 1000 rows; Table IV)."""
+    import json
+    from paper_2506_20677_gb300.selector import train_trees as tt
+    labels = os.path.join(ROOT, "paper_2506_20677_gb300", "selector", "labels_gb300.json")
+    rows, X, y = tt.load(labels)
+    m = orc.Model(SHIPPED)
+    hit = sum(int(m.predict(list(x)) == int(c)) for x, c in zip(X, y))
+    assert hit >= 0.9 * len(rows), (hit, len(rows))
