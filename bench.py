@@ -37,6 +37,7 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
         "segradix_count": w, "segradix_scatter": 2 * (w + v),
         "bucket_sort_4k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
         "blocksort_single": 2 * (w + v), "copy": 8,
+        "msd_scatter": 2 * w, "msd_bin_minmax": w,
     }
     return table.get(kernel, 0.0)
 
@@ -51,7 +52,8 @@ def measured_peaks():
 
 
 def kernel_source_hash(kernel: str):
-    files = {"radix": "radix.cu", "sample": "samplesort.cu", "bucket": "blocksort.cuh",
+    files = {"radix": "radix.cu", "sample": "samplesort.cu", "msd": "samplesort.cu",
+             "bucket": "blocksort.cuh",
              "features": "features.cu", "counting": "counting.cu", "copy": "counting.cu"}
     for pre, f in files.items():
         if kernel.startswith(pre):

@@ -82,7 +82,9 @@ void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out) {
 
 ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
                         cudaStream_t st, ahs_features_t* out) {
-    ahs_status rc = ensure_workspace(ctx, features_region(ctx->sms));
+    // Room for the counting sort's prefix too: that strategy reads the
+    // histogram in place, and growing the workspace would not keep it.
+    ahs_status rc = ensure_workspace(ctx, features_region(ctx->sms) + align256((kMaxBins + 1) * 8));
     if (rc != AHS_OK) return rc;
     FeatureScratch s = carve_features(ctx);
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
@@ -164,7 +166,24 @@ ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st) {
     e = cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
-    return code == kDevLookbackTimeout ? AHS_ERR_DEVICE_TIMEOUT : AHS_ERR_CUDA;
+    return (code == kDevLookbackTimeout || code == kDevCopyTimeout) ? AHS_ERR_DEVICE_TIMEOUT
+                                                                     : AHS_ERR_CUDA;
+}
+
+// The feature histogram's nbins counts, copied to the host before the
+// workspace may grow (growing it does not keep its contents).
+static ahs_status host_histogram(ahs_ctx* ctx, const ahs_features_t& f, cudaStream_t st,
+                                 std::vector<unsigned long long>* out) {
+    FeatureScratch fs = carve_features(ctx);
+    ahs_status rc = ensure_stage(ctx, (size_t)f.nbins * 8);
+    if (rc != AHS_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_stage, fs.hist, (size_t)f.nbins * 8,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    out->resize(f.nbins);
+    std::memcpy(out->data(), ctx->h_stage, (size_t)f.nbins * 8);
+    return AHS_OK;
 }
 
 ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kout,
@@ -205,6 +224,17 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
         [[fallthrough]];
     }
     case AHS_RADIX: {
+        if (s == AHS_RADIX && !vin && f.hist_shift > 0 && n >= 2 && n <= 0xffffffffull) {
+            // Keys only: most significant digit first, unstable partitions.
+            std::vector<unsigned long long> hist;
+            ahs_status rc = host_histogram(ctx, f, st, &hist);
+            if (rc != AHS_OK) return rc;
+            const size_t need = samplesort_scratch_bytes(n, kd.bytes, false);
+            rc = ensure_workspace(ctx, freg + need);
+            if (rc != AHS_OK) return rc;
+            return run_msd_radix(ctx, kin, kout, n, kd, min_ord, hist, f.hist_shift,
+                                 static_cast<char*>(ctx->ws) + freg, st, passes, buckets);
+        }
         const RadixPlan plan = radix_plan(f.span);
         if (plan.passes == 0) {
             e = launch_copy32(kout, kin, n * kd.bytes / 4, ctx->sms, st);
@@ -224,12 +254,19 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
         return cuda_status(ctx, e);
     }
     case AHS_GENERAL: {
+        if (n >= (1ull << 32)) return AHS_ERR_UNIMPLEMENTED;
+        std::vector<unsigned long long> hist;
+        const bool use_hist = !vin && f.nbins > 256;
+        if (use_hist) {
+            ahs_status rc = host_histogram(ctx, f, st, &hist);
+            if (rc != AHS_OK) return rc;
+        }
         const size_t need = samplesort_scratch_bytes(n, kd.bytes, vin != nullptr);
         ahs_status rc = ensure_workspace(ctx, freg + need);
         if (rc != AHS_OK) return rc;
-        if (n >= (1ull << 32)) return AHS_ERR_UNIMPLEMENTED;
         return run_samplesort(ctx, kin, kout, vin, vout, n, kd, static_cast<char*>(ctx->ws) + freg,
-                              st, passes, buckets);
+                              st, passes, buckets, use_hist ? &hist : nullptr, min_ord,
+                              f.hist_shift);
     }
     default:
         return AHS_ERR_INVALID_ARG;

@@ -32,6 +32,7 @@ enum DeviceError : uint32_t {
     kDevLookbackTimeout = 1,   // a decoupled look-back wait ran out
     kDevBadState = 2,          // a status word held an impossible value
     kDevOverflow = 3,          // a bucket exceeded the capacity a kernel was sized for
+    kDevCopyTimeout = 4,       // a bulk-async copy did not complete
 };
 
 // Key traits: keys move as their raw bits (K); digits, ranges and histograms
@@ -192,6 +193,104 @@ __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
 }
 __device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------------------------ bulk-async copies
+// One-dimensional bulk copies (cp.async.bulk, the TMA engine) from global into
+// shared memory, completed on an mbarrier that counts the bytes delivered.
+// Source, destination and size must be multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gmem_src, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Order this thread's earlier generic-proxy shared-memory accesses before
+// later bulk-async writes into the same buffer.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Wait for phase `parity` of the barrier; gives up after ~2^22 polls (seconds)
+// and returns false, so a lost copy can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t spin = 0; spin < (1u << 22); ++spin) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async), for the few
+// keys of a run that bulk copies cannot move; completed by cp_async_wait_all
+// in the issuing thread.
+template <typename K>
+__device__ __forceinline__ void cp_async_key(K* smem_dst, const K* gmem_src) {
+    static_assert(sizeof(K) == 4 || sizeof(K) == 8, "4- or 8-byte keys");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(smem_dst)),
+                 "l"(gmem_src), "n"(sizeof(K))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Wait until at most one (the most recent) cp.async group is pending.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Split of a run of `size` keys at p into a head before the first 16-byte
+// boundary, a body that bulk copies can move and a tail.  In a shared-memory
+// buffer whose base is 16-byte aligned, key i of the run goes to
+// buf[pad + i]: the body then starts 16-byte aligned.  The buffer needs
+// size + 16 / sizeof(K) elements.
+template <typename K>
+struct TileSplit {
+    uint32_t head, body, pad;
+    __device__ __forceinline__ TileSplit(const K* p, uint32_t size) {
+        constexpr uint32_t V = 16 / sizeof(K);
+        const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(p) & 15u) / sizeof(K));
+        head = mis ? V - mis : 0;
+        if (head > size) head = size;
+        body = ((size - head) / V) * V;
+        pad = (V - head % V) % V;
+    }
+};
+
+// One thread: start moving a run of `size` keys at src into buf (key i at
+// buf[pad + i]): the body by a bulk copy completing on `bar` (which gets this
+// thread's arrival either way), head and tail by cp.async as one commit group
+// (the same thread waits for it before the block reads the buffer).
+template <typename K>
+__device__ __forceinline__ void issue_run(K* buf, const K* src, uint32_t size, uint64_t* bar,
+                                          uint32_t extra_tx = 0) {
+    const TileSplit<K> sp(src, size);
+    for (uint32_t i = 0; i < sp.head; ++i) cp_async_key(&buf[sp.pad + i], src + i);
+    for (uint32_t i = sp.head + sp.body; i < size; ++i) cp_async_key(&buf[sp.pad + i], src + i);
+    cp_async_commit();
+    const uint32_t tx = sp.body * (uint32_t)sizeof(K) + extra_tx;
+    if (tx) mbar_arrive_expect_tx(bar, tx);
+    else mbar_arrive(bar);
+    if (sp.body) bulk_load(&buf[sp.pad + sp.head], src + sp.head, sp.body * (uint32_t)sizeof(K), bar);
 }
 
 __device__ __forceinline__ void report_error(uint32_t* err, uint32_t code) {

@@ -7,6 +7,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "select.h"
@@ -70,8 +71,22 @@ ahs_status ensure_aux(ahs_ctx* ctx, size_t bytes);
 ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes);
 // General path: stable sample sort with shared-memory bucket sorts.  scratch is
 // samplesort_scratch_bytes() of workspace.  Synchronises `st` once per level.
+// Keys only, with `hist` (the host copy of the feature histogram, bins of
+// (ord(x) - min_ord) >> shift): the first two levels take their splitters from
+// the histogram's bin boundaries (exact bucket sizes, no counting pass).
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
-                          uint32_t* levels_out, uint32_t* buckets_out);
+                          uint32_t* levels_out, uint32_t* buckets_out,
+                          const std::vector<unsigned long long>* hist = nullptr,
+                          uint64_t min_ord = 0, uint32_t shift = 0);
+
+// Keys-only radix sort, most significant digit first: two partition passes by
+// the high and low byte of the feature histogram's bin (exact bucket sizes
+// from `hist`, the host copy of the histogram, bin = (ord(x) - min_ord) >> shift),
+// then per-bin shared-memory sorts.  scratch: samplesort_scratch_bytes().
+ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
+                         uint64_t min_ord, const std::vector<unsigned long long>& hist,
+                         uint32_t shift, void* scratch, cudaStream_t st, uint32_t* levels_out,
+                         uint32_t* buckets_out);
 
 }  // namespace ahs

@@ -42,12 +42,15 @@ constexpr uint32_t kOversample = 32;
 constexpr uint32_t kSamples = (kMaxSplit + 1) * kOversample;   // 8,192
 constexpr uint32_t kChunkTiles = 32;
 constexpr uint32_t kMaxLevels = 16;
+constexpr uint32_t kCopyChunk = 4096;           // keys one CTA copies of an unsorted bucket
 constexpr int kSplit = 0;                       // bucket = splitter interval / equality
 constexpr int kDigit = 1;                       // bucket = 8-bit digit of key - segment min
+constexpr int kRange = 2;                       // bucket = number of splitters below the key
 constexpr int kHistCopies = 4;
 static_assert(kThreads % 32 == 0 && kThreads >= 32, "whole warps");
 static_assert((uint32_t)kThreads * kIpt >= kSamples, "one CTA must hold the whole splitter sample");
 static_assert(kCols % kThreads == 0 || kThreads % kCols == 0, "bucket columns divide the block");
+static_assert(kCols < 1024 && kThreads * kIpt <= (1u << 22), "scatter packs (slot << 10) | bucket");
 
 struct SegDesc {
     unsigned long long begin;
@@ -98,8 +101,16 @@ struct Classifier {
     K mn;
     uint32_t shift;
     __device__ __forceinline__ uint32_t operator()(K o) const {
-        if constexpr (MODE == kSplit) return classify_split(tree, sorted, m, o);
-        else return (uint32_t)((K)(o - mn) >> shift) & 0xffu;
+        if constexpr (MODE == kSplit) {
+            return classify_split(tree, sorted, m, o);
+        } else if constexpr (MODE == kRange) {
+            uint32_t j = 1;
+#pragma unroll
+            for (int l = 0; l < 8; ++l) j = 2 * j + (o > tree[j] ? 1u : 0u);
+            return j - 256;
+        } else {
+            return (uint32_t)((K)(o - mn) >> shift) & 0xffu;
+        }
     }
 };
 
@@ -152,8 +163,10 @@ ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t 
     if (threadIdx.x == 0) nsplit[blockIdx.x] = total;
 }
 
-// Per tile: bucket histogram (4 copies spread the atomics of skewed inputs).
-template <typename K, int MODE>
+// Per tile: bucket histogram (4 copies spread the atomics of skewed inputs),
+// written as one row of the tiles x buckets matrix, or (TOTALS) added into the
+// segment's bucket totals.
+template <typename K, int MODE, bool TOTALS>
 __global__ void __launch_bounds__(kThreads)
 ss_count(const K* __restrict__ src, const TileDesc* __restrict__ tiles,
          const SegDesc* __restrict__ segs, const K* __restrict__ splitters,
@@ -182,8 +195,27 @@ ss_count(const K* __restrict__ src, const TileDesc* __restrict__ tiles,
         if (AHS_DCHECK(b < kCols, "count bucket", b)) atomicAdd(&mine[b], 1u);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kCols; i += kThreads)
-        counts[(size_t)blockIdx.x * kCols + i] = hist[0][i] + hist[1][i] + hist[2][i] + hist[3][i];
+    for (uint32_t i = threadIdx.x; i < kCols; i += kThreads) {
+        const uint32_t c = hist[0][i] + hist[1][i] + hist[2][i] + hist[3][i];
+        if constexpr (TOTALS) {
+            if (c) atomicAdd(&counts[(size_t)t.seg * kCols + i], c);
+        } else {
+            counts[(size_t)blockIdx.x * kCols + i] = c;
+        }
+    }
+}
+
+// Per segment: exclusive scan of the bucket totals; the bases seed the
+// scatter's per-bucket cursors.
+__global__ void __launch_bounds__(kCols)
+ss_scan_totals(const uint32_t* __restrict__ seg_tot, uint32_t* __restrict__ seg_base,
+               uint32_t* __restrict__ cursor) {
+    __shared__ uint32_t scratch[kCols / 32 + 1];
+    const size_t at = (size_t)blockIdx.x * kCols + threadIdx.x;
+    uint32_t total;
+    const uint32_t base = block_exclusive_scan<kCols>(seg_tot[at], scratch, &total);
+    seg_base[at] = base;
+    cursor[at] = base;
 }
 
 // Segmented column scan of the tiles x buckets count matrix, in three steps:
@@ -341,6 +373,179 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
     }
 }
 
+// ------------------------------------------------------------ keys-only scatter
+//
+// Without a payload the order of equal-bucket keys inside a bucket is free (the
+// bucket is sorted afterwards), so the scatter need not be stable.  Each CTA is
+// persistent and walks the tile list with a stride of the grid; tile k+2G is
+// fetched into shared memory by the bulk-async copy engine while tiles k and
+// k+G are processed.  A key's slot in its tile's bucket run is one returning
+// shared-memory atomic; the tile's run of each bucket is placed by one global
+// atomic on the bucket's cursor (no cross-tile prefix is needed); the tile is
+// staged in bucket order and written out in coalesced runs.
+constexpr int kFastThreads = 512;
+static_assert(kFastThreads == (int)kCols, "one bucket column per thread");
+
+template <typename K>
+struct FastCfg {
+    static constexpr int kIpt = sizeof(K) == 4 ? 16 : 8;
+    static constexpr uint32_t kTileKeys = kFastThreads * kIpt;   // 32 KiB of keys
+    static constexpr uint32_t kVec = 16 / sizeof(K);               // keys per 16 bytes
+};
+
+template <typename K>
+struct FastSmem {
+    static constexpr uint32_t TILE = FastCfg<K>::kTileKeys;
+    K buf[2][TILE + FastCfg<K>::kVec];
+    K sp[2][2 * kSlots];   // splitters of the tile in buf[s] (sample-sort levels)
+    uint16_t bid[TILE];
+    uint32_t hist[kCols];
+    uint32_t tile_start[kCols];
+    uint32_t gbase[kCols];
+    uint32_t scan[kFastThreads / 32 + 1];
+    uint64_t bar[2];
+};
+
+template <typename K, int MODE>
+__global__ void __launch_bounds__(kFastThreads, 2)
+ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* __restrict__ tiles,
+                uint32_t ntiles, const SegDesc* __restrict__ segs, const K* __restrict__ splitters,
+                const uint32_t* __restrict__ nsplit, K flip, uint32_t shift,
+                uint32_t* __restrict__ cursor, uint32_t* __restrict__ err) {
+    constexpr int IPT = FastCfg<K>::kIpt;
+    constexpr uint32_t TILE = FastCfg<K>::kTileKeys;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FastSmem<K>& S = *reinterpret_cast<FastSmem<K>*>(smem_raw);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t G = gridDim.x;
+
+    constexpr uint32_t kSpBytes = 2 * kSlots * (uint32_t)sizeof(K);
+    auto issue = [&](int s, uint32_t k) {   // thread 0
+        if (k >= ntiles) { cp_async_commit(); return; }   // keep one group per issue
+        const TileDesc t = tiles[k];
+        issue_run(S.buf[s], src + t.begin, t.size, &S.bar[s], MODE != kDigit ? kSpBytes : 0u);
+        if constexpr (MODE != kDigit)
+            bulk_load(S.sp[s], splitters + (size_t)t.seg * 2 * kSlots, kSpBytes, &S.bar[s]);
+    };
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_init_fence();
+        issue(0, blockIdx.x);
+        issue(1, blockIdx.x + G);
+    }
+    for (uint32_t j = tid; j < kCols; j += kFastThreads) S.hist[j] = 0;
+    __syncthreads();
+
+    Classifier<K, MODE> cls{};
+    uint32_t parity = 0;   // bit s: phase of buffer s's barrier
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t k = blockIdx.x + it * G;
+        if (k >= ntiles) break;
+        const int s = it & 1;
+        const TileDesc t = tiles[k];
+        const SegDesc sg = segs[t.seg];
+        const TileSplit<K> sp(src + t.begin, t.size);
+        K* buf = S.buf[s];
+        if constexpr (MODE != kDigit) {
+            cls.tree = S.sp[s];
+            cls.sorted = S.sp[s] + kSlots;
+            if constexpr (MODE == kSplit) cls.m = nsplit[t.seg];
+        } else {
+            cls.mn = (K)sg.min_ord;
+            cls.shift = shift;
+        }
+        if (!mbar_wait(&S.bar[s], (parity >> s) & 1u)) report_error(err, kDevCopyTimeout);
+        parity ^= 1u << s;
+        if (tid == 0) cp_async_wait_prior();   // head and tail keys of this tile
+        __syncthreads();
+
+        // Bucket of each key and its slot in the tile's run of that bucket.
+        // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
+        K key[IPT];
+        uint32_t br[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint32_t p = i * kFastThreads + tid;
+            br[i] = kCols;
+            if (p < t.size) {
+                key[i] = buf[sp.pad + p];
+                const uint32_t b = cls((K)(key[i] ^ flip));
+                br[i] = (atomicAdd(&S.hist[b], 1u) << 10) | b;
+            }
+        }
+        __syncthreads();
+
+        // Reserve each bucket's run in the segment; tile-local run starts.
+        {
+            const uint32_t j = tid;   // kFastThreads == kCols
+            const uint32_t c = S.hist[j];
+            S.hist[j] = 0;
+            const uint32_t base = c ? atomicAdd(&cursor[(size_t)t.seg * kCols + j], c) : 0u;
+            uint32_t total;
+            const uint32_t ex = block_exclusive_scan<kFastThreads>(c, S.scan, &total);
+            S.tile_start[j] = ex;
+            S.gbase[j] = base - ex;
+        }
+        __syncthreads();
+
+        // Stage in bucket order (the tile's keys are all in registers now).
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint32_t b = br[i] & 1023u;
+            if (b < kCols) {
+                const uint32_t lp = S.tile_start[b] + (br[i] >> 10);
+                if (AHS_DCHECK(lp < t.size, "fast scatter stage", lp)) {
+                    buf[lp] = key[i];
+                    S.bid[lp] = (uint16_t)b;
+                }
+            }
+        }
+        __syncthreads();
+
+        K* out = dst + sg.begin;
+#pragma unroll 4
+        for (uint32_t j = tid; j < t.size; j += kFastThreads) {
+            const uint32_t gp = S.gbase[S.bid[j]] + j;
+            if (gp >= sg.size) { report_error(err, kDevBadState); continue; }
+            out[gp] = buf[j];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            issue(s, k + 2 * G);
+        }
+    }
+}
+
+// Per tile of the list: min and max of ord(x), folded into the tile's
+// segment slot (mm[2 s] = min, mm[2 s + 1] = max; the host seeds them).
+template <typename K>
+__global__ void __launch_bounds__(kThreads)
+seg_tile_minmax(const K* __restrict__ src, const TileDesc* __restrict__ tiles, K flip,
+                unsigned long long* __restrict__ mm) {
+    __shared__ unsigned long long s_mn[kThreads / 32], s_mx[kThreads / 32];
+    const TileDesc t = tiles[blockIdx.x];
+    K mn = ~K(0), mx = 0;
+    for (uint32_t i = threadIdx.x; i < t.size; i += kThreads) {
+        const K o = src[t.begin + i] ^ flip;
+        mn = o < mn ? o : mn;
+        mx = o > mx ? o : mx;
+    }
+    unsigned long long a = warp_min((unsigned long long)mn), b = warp_max((unsigned long long)mx);
+    const uint32_t warp = threadIdx.x >> 5;
+    if (lane_id() == 0) { s_mn[warp] = a; s_mx[warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) {
+            a = s_mn[w] < a ? s_mn[w] : a;
+            b = s_mx[w] > b ? s_mx[w] : b;
+        }
+        atomicMin(&mm[2 * t.seg], a);
+        atomicMax(&mm[2 * t.seg + 1], b);
+    }
+}
+
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename F>
@@ -361,11 +566,12 @@ struct Level {
     uint32_t* chunk_sum = nullptr;
     uint32_t* seg_tot = nullptr;
     uint32_t* seg_base = nullptr;
+    uint32_t* cursor = nullptr;
     void* splitters = nullptr;
     uint32_t* nsplit = nullptr;
 };
 
-void build_lists(const std::vector<SegRange>& open, Level& L) {
+void build_lists(const std::vector<SegRange>& open, Level& L, uint32_t tile_keys = kTile) {
     L.segs.clear();
     L.tiles.clear();
     L.chunks.clear();
@@ -375,11 +581,11 @@ void build_lists(const std::vector<SegRange>& open, Level& L) {
         sd.size = open[s].size;
         sd.min_ord = open[s].min_ord;
         sd.first_chunk = (uint32_t)L.chunks.size();
-        const uint32_t nt = (uint32_t)ceil_div(sd.size, kTile);
+        const uint32_t nt = (uint32_t)ceil_div(sd.size, tile_keys);
         const uint32_t t0 = (uint32_t)L.tiles.size();
         for (uint32_t t = 0; t < nt; ++t) {
-            const uint32_t off = t * kTile;
-            L.tiles.push_back({sd.begin + off, std::min(kTile, sd.size - off), s});
+            const uint32_t off = t * tile_keys;
+            L.tiles.push_back({sd.begin + off, std::min(tile_keys, sd.size - off), s});
         }
         for (uint32_t t = 0; t < nt; t += kChunkTiles)
             L.chunks.push_back({t0 + t, std::min(kChunkTiles, nt - t), s, 0});
@@ -397,7 +603,7 @@ ahs_status upload_level(ahs_ctx* ctx, Level& L, uint32_t key_bytes, bool split, 
     const size_t b_counts = a256(nt * kCols * 4), b_csum = a256(nc * kCols * 4),
                  b_seg = a256(ns * kCols * 4), b_spl = split ? a256(ns * 2 * kSlots * key_bytes) : 0,
                  b_ns = a256(ns * 4);
-    ahs_status rc = ensure_aux(ctx, b_segs + b_tiles + b_chunks + b_counts + b_csum + 2 * b_seg +
+    ahs_status rc = ensure_aux(ctx, b_segs + b_tiles + b_chunks + b_counts + b_csum + 3 * b_seg +
                                         b_spl + b_ns);
     if (rc == AHS_OK) rc = ensure_stage(ctx, b_segs + b_tiles + b_chunks);
     if (rc != AHS_OK) return rc;
@@ -409,6 +615,7 @@ ahs_status upload_level(ahs_ctx* ctx, Level& L, uint32_t key_bytes, bool split, 
     L.chunk_sum = reinterpret_cast<uint32_t*>(p); p += b_csum;
     L.seg_tot = reinterpret_cast<uint32_t*>(p); p += b_seg;
     L.seg_base = reinterpret_cast<uint32_t*>(p); p += b_seg;
+    L.cursor = reinterpret_cast<uint32_t*>(p); p += b_seg;
     L.splitters = split ? p : nullptr; p += b_spl;
     L.nsplit = reinterpret_cast<uint32_t*>(p);
     char* hs = static_cast<char*>(ctx->h_stage);
@@ -420,10 +627,13 @@ ahs_status upload_level(ahs_ctx* ctx, Level& L, uint32_t key_bytes, bool split, 
     return cuda_status(ctx, e);
 }
 
-// One stable partition of every segment of the level, src -> dst.
+// One partition of every segment of the level, src -> dst: stable with a
+// payload (count matrix, segmented column scan, ranked scatter), unstable
+// without (bucket totals, cursors, persistent scatter) -- FAST, keys only.
 template <typename K, bool VALS, int MODE>
 cudaError_t partition(const Level& L, const K* src, K* dst, const uint32_t* vsrc, uint32_t* vdst,
-                      K flip, uint32_t level, uint32_t shift, bool totals, cudaStream_t st) {
+                      K flip, uint32_t level, uint32_t shift, bool totals, cudaStream_t st,
+                      bool fast = false, int sms = kDefaultSms, uint32_t* err = nullptr) {
     const uint32_t ns = (uint32_t)L.segs.size(), nt = (uint32_t)L.tiles.size(),
                    nc = (uint32_t)L.chunks.size();
     uint64_t keys = 0;
@@ -434,10 +644,30 @@ cudaError_t partition(const Level& L, const K* src, K* dst, const uint32_t* vsrc
         ss_sample<K><<<ns, kThreads, sizeof(BlockSortSmem<K, false, kThreads, kIpt>), st>>>(
             src, L.d_segs, level, flip, spl, L.nsplit);
     }
+    if (!VALS && fast) {
+        cudaError_t e = cudaMemsetAsync(L.seg_tot, 0, (size_t)ns * kCols * 4, st);
+        if (e != cudaSuccess) return e;
+        {
+            TraceScope ts(MODE == kSplit ? "sample_count" : "segradix_count", keys, st);
+            ss_count<K, MODE, true><<<nt, kThreads, 0, st>>>(src, L.d_tiles, L.d_segs, spl,
+                                                             L.nsplit, flip, shift, L.seg_tot);
+        }
+        {
+            TraceScope ts(MODE == kSplit ? "sample_scan" : "segradix_scan", ns, st);
+            ss_scan_totals<<<ns, kCols, 0, st>>>(L.seg_tot, L.seg_base, L.cursor);
+        }
+        {
+            const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)sms);
+            TraceScope ts(MODE == kSplit ? "sample_scatter" : "segradix_scatter", keys, st);
+            ss_scatter_keys<K, MODE><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                src, dst, L.d_tiles, nt, L.d_segs, spl, L.nsplit, flip, shift, L.cursor, err);
+        }
+        return cudaGetLastError();
+    }
     {
         TraceScope ts(MODE == kSplit ? "sample_count" : "segradix_count", keys, st);
-        ss_count<K, MODE><<<nt, kThreads, 0, st>>>(src, L.d_tiles, L.d_segs, spl, L.nsplit, flip,
-                                                   shift, L.counts);
+        ss_count<K, MODE, false><<<nt, kThreads, 0, st>>>(src, L.d_tiles, L.d_segs, spl, L.nsplit,
+                                                          flip, shift, L.counts);
     }
     {
         TraceScope ts(MODE == kSplit ? "sample_scan" : "segradix_scan", nt, st);
@@ -459,6 +689,9 @@ cudaError_t set_attrs() {
     cudaError_t e = set_smem(ss_sample<K>, sizeof(BlockSortSmem<K, false, kThreads, kIpt>));
     if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kSplit>, sizeof(ScatterSmem<K, VALS>));
     if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kDigit>, sizeof(ScatterSmem<K, VALS>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kSplit>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kRange>, sizeof(FastSmem<K>));
     return e;
 }
 
@@ -471,11 +704,19 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
     std::vector<FinalBucket> cls[kBucketClasses];
     uint32_t nsorted = 0;
     for (const FinalBucket& f : finals) {
+        if (!f.sort && f.size > kCopyChunk) {
+            // A large copy (an equality bucket of a heavy key) is split so
+            // that many CTAs share it.
+            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
+                cls[0].push_back({f.begin + o, std::min(kCopyChunk, f.size - o), f.where, 0, 0});
+            continue;
+        }
         cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
         nsorted += f.sort;
     }
+    size_t nf = 0;
+    for (int k = 0; k < kBucketClasses; ++k) nf += cls[k].size();
     if (sorted) *sorted = nsorted;
-    const size_t nf = finals.size();
     if (nf == 0) return AHS_OK;
     ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
     if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
@@ -497,7 +738,7 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
     cudaError_t e = cudaMemcpyAsync(df, hf, nf * sizeof(FinalBucket), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
-                                 vtmp, vout, vin, vout, kd, st);
+                                 vtmp, vout, vin, vout, kd, st, ctx->sms, ctx->d_err);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
 }
@@ -533,10 +774,11 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
         K* dst = (level % 2 == 1) ? ktmp : kout;
         uint32_t* vdst = (level % 2 == 1) ? vtmp : vout;
         const uint8_t where = (level % 2 == 1) ? 0 : 1;
-        build_lists(open, L);
+        build_lists(open, L, VALS ? kTile : FastCfg<K>::kTileKeys);
         ahs_status rc = upload_level(ctx, L, sizeof(K), true, st);
         if (rc != AHS_OK) return rc;
-        e = partition<K, VALS, kSplit>(L, src, dst, vsrc, vdst, flip, level, 0, true, st);
+        e = partition<K, VALS, kSplit>(L, src, dst, vsrc, vdst, flip, level, 0, true, st, !VALS,
+                                       ctx->sms, ctx->d_err);
         const size_t ns = L.segs.size(), bread = ns * kCols * 4;
         if (e == cudaSuccess) rc = ensure_stage(ctx, 2 * bread);
         if (rc != AHS_OK) return rc;
@@ -599,6 +841,310 @@ ahs_status radix_segs_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin
     return AHS_OK;
 }
 
+// ------------------------------------------------------------ MSD radix (keys only)
+//
+// The feature pass leaves the exact histogram of the top 16 bits of
+// u = ord(x) - min (bin = u >> s, s = bitlen(span) - 16).  Two partition
+// passes by the bin's high and low byte -- whose bucket sizes are therefore
+// known without a counting pass -- leave every bin's keys at their final
+// position; a bin then holds keys that differ only in their low s bits and is
+// finished by the shared-memory sort (or, above its capacity, checked for a
+// single value and otherwise handed to the sample sort).
+
+// Upload segments, tiles and host-computed cursors of one pass into ctx->aux.
+ahs_status upload_msd(ahs_ctx* ctx, Level& L, const std::vector<uint32_t>& cursor, cudaStream_t st,
+                      const void* splitters = nullptr, size_t splitter_bytes = 0) {
+    const size_t ns = L.segs.size(), nt = L.tiles.size();
+    const size_t b_segs = a256(ns * sizeof(SegDesc)), b_tiles = a256(nt * sizeof(TileDesc)),
+                 b_cur = a256(cursor.size() * 4), b_spl = a256(splitter_bytes);
+    const size_t total = b_segs + b_tiles + b_cur + b_spl;
+    ahs_status rc = ensure_aux(ctx, total);
+    if (rc == AHS_OK) rc = ensure_stage(ctx, total);
+    if (rc != AHS_OK) return rc;
+    char* p = static_cast<char*>(ctx->aux);
+    L.d_segs = reinterpret_cast<SegDesc*>(p);
+    L.d_tiles = reinterpret_cast<TileDesc*>(p + b_segs);
+    L.cursor = reinterpret_cast<uint32_t*>(p + b_segs + b_tiles);
+    L.splitters = splitter_bytes ? p + b_segs + b_tiles + b_cur : nullptr;
+    char* hs = static_cast<char*>(ctx->h_stage);
+    std::memcpy(hs, L.segs.data(), ns * sizeof(SegDesc));
+    std::memcpy(hs + b_segs, L.tiles.data(), nt * sizeof(TileDesc));
+    if (!cursor.empty()) std::memcpy(hs + b_segs + b_tiles, cursor.data(), cursor.size() * 4);
+    if (splitter_bytes) std::memcpy(hs + b_segs + b_tiles + b_cur, splitters, splitter_bytes);
+    cudaError_t e = cudaMemcpyAsync(p, hs, total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(ctx, e);
+}
+
+// Host: splitter table of one segment for the range classifier (tree[1..255]
+// then the 256 sorted values, padded with the largest value) from up to 255
+// increasing ord-space thresholds: a key o goes to bucket #{t : o > t}.
+template <typename K>
+void range_splitters(const std::vector<K>& thr, K* out) {
+    K sorted[kSlots];
+    for (uint32_t j = 0; j < kSlots; ++j) sorted[j] = j < thr.size() ? thr[j] : ~K(0);
+    out[0] = 0;
+    for (uint32_t j = 1; j < kSlots; ++j) {
+        uint32_t d = 0;
+        while ((2u << d) <= j) ++d;                     // depth of node j
+        const uint32_t p = j - (1u << d);
+        out[j] = sorted[((2 * p + 1) << (7 - d)) - 1];
+    }
+    for (uint32_t j = 0; j < kSlots; ++j) out[kSlots + j] = sorted[j];
+}
+
+// Host: greedy grouping of bins [b0, b1) into at most 256 runs of about
+// `target` keys (a bin heavier than that is a run of its own).  Returns the
+// first bin of every run after the first.
+std::vector<uint32_t> group_bins(const std::vector<unsigned long long>& hist, uint32_t b0,
+                                 uint32_t b1, unsigned long long target) {
+    std::vector<uint32_t> starts;
+    unsigned long long acc = 0;
+    for (uint32_t b = b0; b < b1; ++b) {
+        if (acc > 0 && acc + hist[b] > target && starts.size() < kSlots - 1) {
+            starts.push_back(b);
+            acc = 0;
+        }
+        acc += hist[b];
+    }
+    return starts;
+}
+
+// Runs of the output larger than one CTA sorts, each the keys of one or a few
+// histogram bins: a min / max pass drops those holding a single value, the
+// rest are sorted in place by the sample sort.
+template <typename K>
+ahs_status finish_large(ahs_ctx* ctx, const std::vector<SegRange>& large, K* kout, uint64_t n,
+                        K flip, void* scratch, cudaStream_t st, uint32_t* levels_out,
+                        uint32_t* buckets_out) {
+    if (large.empty()) return AHS_OK;
+    K* ktmp = static_cast<K*>(scratch);
+    Level L;
+    std::vector<SegRange> multi;
+    build_lists(large, L, kTile);
+    ahs_status rc = upload_msd(ctx, L, {}, st);
+    if (rc != AHS_OK) return rc;
+    const size_t ns = large.size();
+    // The temporary buffer is free here: it holds the min / max slots.
+    unsigned long long* d_mm = reinterpret_cast<unsigned long long*>(ktmp);
+    std::vector<unsigned long long> seed(2 * ns);
+    for (size_t q = 0; q < ns; ++q) { seed[2 * q] = ~0ull; seed[2 * q + 1] = 0ull; }
+    rc = ensure_stage(ctx, 2 * ns * 8);
+    if (rc != AHS_OK) return rc;
+    std::memcpy(ctx->h_stage, seed.data(), 2 * ns * 8);
+    cudaError_t e = cudaMemcpyAsync(d_mm, ctx->h_stage, 2 * ns * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        uint64_t lk = 0;
+        for (const SegRange& x : large) lk += x.size;
+        TraceScope ts("msd_bin_minmax", lk, st);
+        seg_tile_minmax<K><<<(uint32_t)L.tiles.size(), kThreads, 0, st>>>(kout, L.d_tiles, flip, d_mm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_stage, d_mm, 2 * ns * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    const unsigned long long* mm = static_cast<const unsigned long long*>(ctx->h_stage);
+    for (size_t q = 0; q < ns; ++q)
+        if (mm[2 * q] != mm[2 * q + 1]) multi.push_back({large[q].begin, large[q].size, mm[2 * q]});
+    if (multi.empty()) return AHS_OK;
+    uint32_t lv = 0, bk = 0;
+    rc = general_t<K, false>(ctx, kout, kout, nullptr, nullptr, n, multi, {}, flip, scratch, st, &lv, &bk);
+    *levels_out += lv;
+    *buckets_out += bk;
+    return rc;
+}
+
+template <typename K>
+ahs_status msd_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
+                 const std::vector<unsigned long long>& hist, uint32_t shift, void* scratch,
+                 cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
+    K* ktmp = static_cast<K*>(scratch);
+    cudaError_t e = set_attrs<K, false>();
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    constexpr uint32_t TK = FastCfg<K>::kTileKeys;
+    const uint32_t nbins = (uint32_t)hist.size();
+    ahs_status rc = AHS_OK;
+    const uint32_t nb1 = (nbins + 255) / 256;
+    std::vector<unsigned long long> t1(nb1, 0), base1(nb1, 0), binpos(nbins, 0);
+    unsigned long long run = 0;
+    for (uint32_t i = 0; i < nbins; ++i) {
+        binpos[i] = run;
+        run += hist[i];
+        t1[i >> 8] += hist[i];
+    }
+    if (run != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
+    for (uint32_t b = 0, r = 0; b < nb1; ++b) { base1[b] = r; r += (uint32_t)t1[b]; }
+
+    Level L;
+    // Pass 1: high byte of the bin, input -> temporary.
+    {
+        build_lists({SegRange{0ull, (uint32_t)n, (unsigned long long)mn}}, L, TK);
+        std::vector<uint32_t> cur(kCols, 0);
+        for (uint32_t b = 0; b < nb1; ++b) cur[b] = (uint32_t)base1[b];
+        rc = upload_msd(ctx, L, cur, st);
+        if (rc != AHS_OK) return rc;
+        const uint32_t nt = (uint32_t)L.tiles.size();
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
+        TraceScope ts("msd_scatter", n, st);
+        ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+            kin, ktmp, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift + 8, L.cursor,
+            ctx->d_err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+    }
+    // Pass 2: low byte of the bin within each high-byte bucket, temporary -> output.
+    {
+        std::vector<SegRange> segs;
+        std::vector<uint32_t> which;
+        for (uint32_t b = 0; b < nb1; ++b) {
+            if (t1[b] == 0) continue;
+            segs.push_back({base1[b], (uint32_t)t1[b], (unsigned long long)mn});
+            which.push_back(b);
+        }
+        build_lists(segs, L, TK);
+        std::vector<uint32_t> cur(segs.size() * kCols, 0);
+        for (size_t q = 0; q < segs.size(); ++q) {
+            const uint32_t b = which[q];
+            for (uint32_t j = 0; j < 256 && b * 256 + j < nbins; ++j)
+                cur[q * kCols + j] = (uint32_t)(binpos[b * 256 + j] - base1[b]);
+        }
+        rc = upload_msd(ctx, L, cur, st);
+        if (rc != AHS_OK) return rc;
+        const uint32_t nt = (uint32_t)L.tiles.size();
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
+        TraceScope ts("msd_scatter", n, st);
+        ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+            ktmp, kout, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift, L.cursor,
+            ctx->d_err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+    }
+    *levels_out = 2;
+    if (shift == 0) return AHS_OK;   // bins are single values: done
+
+    // Bins: sort in shared memory, or (large) test for a single value first.
+    std::vector<FinalBucket> finals;
+    std::vector<SegRange> large;
+    for (uint32_t i = 0; i < nbins; ++i) {
+        if (hist[i] < 2) continue;
+        if (hist[i] <= kBucketCap) finals.push_back({binpos[i], (uint32_t)hist[i], 1, 1, 0});
+        else large.push_back({binpos[i], (uint32_t)hist[i], 0ull});
+    }
+    rc = finish_buckets(ctx, finals, ktmp, kout, kin, nullptr, nullptr, nullptr,
+                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+    if (rc != AHS_OK || large.empty()) return rc;
+    return finish_large<K>(ctx, large, kout, n, flip, scratch, st, levels_out, buckets_out);
+}
+
+// ------------------------------------------------------- general path, keys only
+//
+// The feature pass leaves the exact histogram of the top 16 bits of
+// u = ord(x) - min; its bin boundaries are splitters whose bucket sizes are
+// known exactly.  Level 1 cuts the bins into <= 256 runs of about n / 256 keys,
+// level 2 cuts every run into runs of about half a CTA's capacity, both with
+// the splitter classifier and no counting pass.  A bin heavier than its run
+// target is a bucket of its own; such buckets (no finer information in the
+// histogram) go on to sampled splitters.
+template <typename K>
+ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
+                          const std::vector<unsigned long long>& hist, uint32_t shift,
+                          void* scratch, cudaStream_t st, uint32_t* levels_out,
+                          uint32_t* buckets_out) {
+    K* ktmp = static_cast<K*>(scratch);
+    cudaError_t e = set_attrs<K, false>();
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    constexpr uint32_t TK = FastCfg<K>::kTileKeys;
+    const uint32_t nbins = (uint32_t)hist.size();
+    std::vector<unsigned long long> binpos(nbins + 1, 0);
+    for (uint32_t i = 0; i < nbins; ++i) binpos[i + 1] = binpos[i] + hist[i];
+    if (binpos[nbins] != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
+    // Keys of bin >= b are exactly those with ord(x) > thr(b).
+    auto thr = [&](uint32_t b) { return (K)(mn + ((K)b << shift) - 1); };
+    auto run = [&](const K* src, K* dst, const std::vector<SegRange>& segs,
+                   const std::vector<std::vector<uint32_t>>& starts) -> ahs_status {
+        Level L;
+        build_lists(segs, L, TK);
+        std::vector<uint32_t> cur(segs.size() * kCols, 0);
+        std::vector<K> spl(segs.size() * 2 * kSlots);
+        for (size_t q = 0; q < segs.size(); ++q) {
+            std::vector<K> t;
+            const std::vector<uint32_t>& st_q = starts[q];
+            const uint32_t first = (uint32_t)(segs[q].min_ord);   // first bin of the segment
+            cur[q * kCols] = 0;
+            for (size_t j = 0; j < st_q.size(); ++j) {
+                t.push_back(thr(st_q[j]));
+                cur[q * kCols + j + 1] = (uint32_t)(binpos[st_q[j]] - binpos[first]);
+            }
+            range_splitters<K>(t, spl.data() + q * 2 * kSlots);
+        }
+        // min_ord carried the first bin for the host only; the classifier needs none.
+        for (SegDesc& sd : L.segs) sd.min_ord = 0;
+        ahs_status rc = upload_msd(ctx, L, cur, st, spl.data(), spl.size() * sizeof(K));
+        if (rc != AHS_OK) return rc;
+        const uint32_t nt = (uint32_t)L.tiles.size();
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
+        uint64_t keys = 0;
+        for (const SegRange& x : segs) keys += x.size;
+        TraceScope ts("sample_scatter", keys, st);
+        ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+            src, dst, L.d_tiles, nt, L.d_segs, static_cast<const K*>(L.splitters), nullptr, flip, 0,
+            L.cursor, ctx->d_err);
+        return cuda_status(ctx, cudaGetLastError());
+    };
+
+    // Level 1: input -> temporary.
+    const std::vector<uint32_t> s1 = group_bins(hist, 0, nbins, std::max<unsigned long long>(n / 256, 1));
+    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1});
+    if (rc != AHS_OK) return rc;
+    // Level 2: every multi-bin run above a CTA's capacity, temporary -> output.
+    std::vector<uint32_t> r1{0};
+    r1.insert(r1.end(), s1.begin(), s1.end());
+    r1.push_back(nbins);
+    std::vector<SegRange> segs2;
+    std::vector<std::vector<uint32_t>> starts2;
+    std::vector<FinalBucket> finals;
+    std::vector<SegRange> large;
+    struct Run { uint32_t b0, b1; };
+    std::vector<Run> runs2;
+    for (size_t g = 0; g + 1 < r1.size(); ++g) {
+        const uint32_t b0 = r1[g], b1 = r1[g + 1];
+        const unsigned long long sz = binpos[b1] - binpos[b0];
+        if (sz == 0) continue;
+        if (sz <= kBucketCap || b1 - b0 == 1) {
+            // Sorted (or, if large, first copied) from the temporary buffer.
+            const bool sort = sz <= kBucketCap && sz > 1;
+            finals.push_back({binpos[b0], (uint32_t)sz, 0, (uint8_t)sort, 0});
+            if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
+            continue;
+        }
+        segs2.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
+        starts2.push_back(group_bins(hist, b0, b1, kBucketCap / 2));
+        runs2.push_back({b0, b1});
+    }
+    uint32_t levels = 1;
+    if (!segs2.empty()) {
+        rc = run(ktmp, kout, segs2, starts2);
+        if (rc != AHS_OK) return rc;
+        levels = 2;
+        for (size_t q = 0; q < segs2.size(); ++q) {
+            std::vector<uint32_t> r{runs2[q].b0};
+            r.insert(r.end(), starts2[q].begin(), starts2[q].end());
+            r.push_back(runs2[q].b1);
+            for (size_t j = 0; j + 1 < r.size(); ++j) {
+                const unsigned long long sz = binpos[r[j + 1]] - binpos[r[j]];
+                if (sz < 2) continue;
+                if (sz <= kBucketCap) finals.push_back({binpos[r[j]], (uint32_t)sz, 1, 1, 0});
+                else large.push_back({binpos[r[j]], (uint32_t)sz, 0ull});
+            }
+        }
+    }
+    *levels_out = levels;
+    rc = finish_buckets(ctx, finals, ktmp, kout, kin, nullptr, nullptr, nullptr,
+                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+    if (rc != AHS_OK) return rc;
+    return finish_large<K>(ctx, large, kout, n, flip, scratch, st, levels_out, buckets_out);
+}
+
 }  // namespace
 
 size_t samplesort_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals) {
@@ -649,14 +1195,39 @@ ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const u
     return finish_buckets(ctx, finals, kout, kout, kin, vout, vout, vin, kd, st, nullptr);
 }
 
+ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
+                         uint64_t min_ord, const std::vector<unsigned long long>& hist,
+                         uint32_t shift, void* scratch, cudaStream_t st, uint32_t* levels_out,
+                         uint32_t* buckets_out) {
+    *levels_out = 0;
+    *buckets_out = 0;
+    if (n > 0xffffffffull || hist.empty() || hist.size() > kMaxBins) return AHS_ERR_INVALID_ARG;
+    if (kd.bytes == 4)
+        return msd_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n, (uint32_t)kd.flip,
+                               (uint32_t)min_ord, hist, shift, scratch, st, levels_out,
+                               buckets_out);
+    return msd_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip, min_ord, hist,
+                           shift, scratch, st, levels_out, buckets_out);
+}
+
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
-                          uint32_t* levels_out, uint32_t* buckets_out) {
+                          uint32_t* levels_out, uint32_t* buckets_out,
+                          const std::vector<unsigned long long>* hist, uint64_t min_ord,
+                          uint32_t shift) {
     *levels_out = 0;
     *buckets_out = 0;
     if (n <= kBucketCap) {
         *buckets_out = 1;
         return cuda_status(ctx, launch_blocksort_single(kin, kout, vin, vout, n, kd, st));
+    }
+    if (!vin && hist && hist->size() > 256 && n <= 0xffffffffull) {
+        if (kd.bytes == 4)
+            return general_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n,
+                                            (uint32_t)kd.flip, (uint32_t)min_ord, *hist, shift,
+                                            scratch, st, levels_out, buckets_out);
+        return general_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip,
+                                        min_ord, *hist, shift, scratch, st, levels_out, buckets_out);
     }
     std::vector<SegRange> segs{{0ull, (uint32_t)n, 0ull}};
     return run_segmented_general(ctx, kin, kout, vin, vout, n, segs, {}, kd, scratch, st,

@@ -16,19 +16,26 @@ def ahs():
 
 
 def test_lookback_timeout_reported_and_context_survives(ahs):
+    # A payload keeps the radix path on its stable LSD passes, whose tiles
+    # chain through the decoupled look-back that the debug flag starves.
     rng = np.random.default_rng(1)
     a = rng.integers(0, 2**32, size=1 << 20, dtype=np.uint32)
+    v = np.arange(a.size, dtype=np.uint32)
     with ahs.Context(0, debug_flags=ahs.AHS_DEBUG_STALL_ONE_TILE) as bad:
         with pytest.raises(ahs.AhsError) as e:
-            bad.sort(dev(a), force=ahs.AHS_RADIX, key_type=ahs.AHS_U32)
+            bad.sort(dev(a), dev(v), force=ahs.AHS_RADIX, key_type=ahs.AHS_U32)
         assert e.value.status == ahs.AHS_ERR_DEVICE_TIMEOUT
-        # the same context keeps working on a path without look-back
+        # the same context keeps working on paths without look-back
         b = rng.integers(0, 1000, size=1 << 20, dtype=np.uint32)
         r = bad.sort(dev(b), force=ahs.AHS_COUNTING, key_type=ahs.AHS_U32)
         assert np.array_equal(host(r.keys, np.uint32), np.sort(b))
-    with ahs.Context(0) as good:
-        r = good.sort(dev(a), force=ahs.AHS_RADIX, key_type=ahs.AHS_U32)
+        r = bad.sort(dev(a), force=ahs.AHS_RADIX, key_type=ahs.AHS_U32)
         assert np.array_equal(host(r.keys, np.uint32), np.sort(a))
+    with ahs.Context(0) as good:
+        r = good.sort(dev(a), dev(v), force=ahs.AHS_RADIX, key_type=ahs.AHS_U32)
+        order = np.argsort(a, kind="stable")
+        assert np.array_equal(host(r.keys, np.uint32), a[order])
+        assert np.array_equal(host(r.vals, np.uint32), v[order])
 
 
 def test_workspace_limit_reports_oom(ahs):
