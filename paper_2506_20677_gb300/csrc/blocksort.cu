@@ -45,80 +45,6 @@ bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1
     }
 }
 
-// Keys only, persistent: CTA c sorts buckets c, c + G, c + 2G, ... of one
-// size class; while it sorts one bucket the bulk-async copy engine brings the
-// next into the other half of a double buffer, so the load latency of a
-// bucket is hidden behind the sort of the previous one.  The buffer a bucket
-// arrived in is also its staging area between passes.
-template <typename K, int T, int IPT>
-struct PersistSmem {
-    static constexpr uint32_t CAP = T * IPT;
-    K buf[2][CAP + 16 / sizeof(K)];
-    BlockSortScratch<K, false, T, IPT> S;
-    uint64_t bar[2];
-};
-
-template <typename K, int T, int IPT>
-__global__ void __launch_bounds__(T)
-bucket_sort_persist(const FinalBucket* __restrict__ list, uint32_t count, const K* buf0,
-                    const K* buf1, const K* buf2, K* out, K flip, uint32_t* __restrict__ err) {
-    constexpr int WARP_ITEMS = 32 * IPT;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& P = *reinterpret_cast<PersistSmem<K, T, IPT>*>(smem_raw);
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const uint32_t wbase = warp * WARP_ITEMS;
-    const uint32_t G = gridDim.x;
-    auto source = [&](const FinalBucket& b) {
-        return (b.where == 0 ? buf0 : (b.where == 1 ? buf1 : buf2)) + b.begin;
-    };
-    auto issue = [&](int s, uint32_t k) {   // thread 0
-        if (k >= count) { cp_async_commit(); return; }   // keep one group per issue
-        const FinalBucket b = list[k];
-        issue_run(P.buf[s], source(b), b.size <= P.CAP ? b.size : 0u, &P.bar[s]);
-    };
-    if (tid == 0) {
-        mbar_init(&P.bar[0], 1);
-        mbar_init(&P.bar[1], 1);
-        mbar_init_fence();
-        issue(0, blockIdx.x);
-        issue(1, blockIdx.x + G);
-    }
-    __syncthreads();
-    uint32_t parity = 0;
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t k = blockIdx.x + it * G;
-        if (k >= count) break;
-        const int s = it & 1;
-        const FinalBucket b = list[k];
-        const TileSplit<K> sp(source(b), b.size);
-        K* buf = P.buf[s];
-        if (!mbar_wait(&P.bar[s], (parity >> s) & 1u)) report_error(err, kDevCopyTimeout);
-        parity ^= 1u << s;
-        if (tid == 0) cp_async_wait_prior();   // head and tail keys of this bucket
-        __syncthreads();
-        const uint32_t m = b.size <= P.CAP ? b.size : 0u;   // larger lists are never built
-        K key[IPT];
-        uint32_t val[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const uint32_t p = wbase + 32 * i + lane;
-            key[i] = p < m ? buf[sp.pad + p] : K(0);
-        }
-        if (b.sort) block_sort_regs<K, false, T, IPT>(key, val, m, flip, P.S, buf, nullptr);
-        K* dst = out + b.begin;
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const uint32_t p = wbase + 32 * i + lane;
-            if (p < m) dst[p] = key[i];
-        }
-        __syncthreads();
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            issue(s, k + 2 * G);
-        }
-    }
-}
-
 template <typename K, bool VALS, int T, int IPT>
 cudaError_t single_t(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint32_t n,
                      K flip, cudaStream_t st) {
@@ -137,21 +63,8 @@ template <typename K, bool VALS, int T, int IPT>
 cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t keys, const void* b0,
                          const void* b1, const void* b2, void* out, const uint32_t* vb0,
                          const uint32_t* vb1, const uint32_t* vb2, uint32_t* vout, K flip,
-                         cudaStream_t st, int sms, uint32_t* err, bool persist) {
+                         cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    if (!VALS && persist) {
-        using PS = PersistSmem<K, T, IPT>;
-        auto fn = bucket_sort_persist<K, T, IPT>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PS));
-        int per_sm = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, sizeof(PS));
-        if (e != cudaSuccess) return e;
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(count, (uint64_t)(per_sm > 0 ? per_sm : 1) * sms);
-        TraceScope ts(T * IPT <= 1024 ? "bucket_sort_1k" : (T * IPT <= 2048 ? "bucket_sort_2k" : (T * IPT <= 4096 ? "bucket_sort_4k" : "bucket_sort_8k")), keys, st);
-        fn<<<grid, T, sizeof(PS), st>>>(d_list, count, static_cast<const K*>(b0), static_cast<const K*>(b1),
-                                        static_cast<const K*>(b2), static_cast<K*>(out), flip, err);
-        return cudaGetLastError();
-    }
     using Smem = BlockSortSmem<K, VALS, T, IPT>;
     auto fn = bucket_finish<K, VALS, T, IPT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -169,20 +82,18 @@ template <typename K, bool VALS>
 cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t counts[kBucketClasses],
                      const uint64_t keys[kBucketClasses], const void* b0, const void* b1, const void* b2,
                      void* out, const uint32_t* vb0, const uint32_t* vb1, const uint32_t* vb2,
-                     uint32_t* vout, K flip, cudaStream_t st, int sms, uint32_t* err) {
-    // Class 0 also carries the copies of unsorted buckets (any size), so it
-    // keeps one CTA per list entry; the sorting classes run persistent.
+                     uint32_t* vout, K flip, cudaStream_t st) {
     cudaError_t e = finish_class<K, VALS, 128, 8>(d_lists[0], counts[0], keys[0], b0, b1, b2, out,
-                                                  vb0, vb1, vb2, vout, flip, st, sms, err, false);
+                                                  vb0, vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
         e = finish_class<K, VALS, 256, 8>(d_lists[1], counts[1], keys[1], b0, b1, b2, out, vb0,
-                                          vb1, vb2, vout, flip, st, sms, err, true);
+                                          vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
         e = finish_class<K, VALS, 256, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
-                                           vb1, vb2, vout, flip, st, sms, err, true);
+                                           vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
         e = finish_class<K, VALS, 512, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
-                                           vb1, vb2, vout, flip, st, sms, err, true);
+                                           vb1, vb2, vout, flip, st);
     return e;
 }
 
@@ -219,17 +130,17 @@ cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
                                  const uint64_t keys[kBucketClasses], const void* buf0, const void* buf1,
                                  const void* buf2, void* out, const uint32_t* vbuf0,
                                  const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
-                                 KeyDesc kd, cudaStream_t st, int sms, uint32_t* err) {
+                                 KeyDesc kd, cudaStream_t st) {
     const bool v = vout != nullptr && vbuf2 != nullptr;
     if (kd.bytes == 4)
         return v ? finish_t<uint32_t, true>(d_lists, counts, keys, buf0, buf1, buf2, out, vbuf0,
-                                           vbuf1, vbuf2, vout, (uint32_t)kd.flip, st, sms, err)
+                                           vbuf1, vbuf2, vout, (uint32_t)kd.flip, st)
                  : finish_t<uint32_t, false>(d_lists, counts, keys, buf0, buf1, buf2, out, nullptr,
-                                            nullptr, nullptr, nullptr, (uint32_t)kd.flip, st, sms, err);
+                                            nullptr, nullptr, nullptr, (uint32_t)kd.flip, st);
     return v ? finish_t<uint64_t, true>(d_lists, counts, keys, buf0, buf1, buf2, out, vbuf0, vbuf1,
-                                       vbuf2, vout, kd.flip, st, sms, err)
+                                       vbuf2, vout, kd.flip, st)
              : finish_t<uint64_t, false>(d_lists, counts, keys, buf0, buf1, buf2, out, nullptr,
-                                        nullptr, nullptr, nullptr, kd.flip, st, sms, err);
+                                        nullptr, nullptr, nullptr, kd.flip, st);
 }
 
 }  // namespace ahs

@@ -13,9 +13,8 @@ namespace ahs {
 
 constexpr int kBsRadix = 256;
 
-// Shared-memory scratch of a block sort, without the key / payload staging.
 template <typename K, bool VALS, int THREADS, int IPT>
-struct BlockSortScratch {
+struct BlockSortSmem {
     static constexpr int W = THREADS / 32;
     static constexpr int CAP = THREADS * IPT;
     uint32_t warp_hist[W][kBsRadix];
@@ -24,36 +23,37 @@ struct BlockSortScratch {
     uint32_t tile_start[kBsRadix];
     uint32_t scan[W + 1];
     unsigned long long red[2][W];
+    K keys[CAP];
+    uint32_t vals[VALS ? CAP : 1];
 };
 
+// Sort keys_in[0..m) (m <= CAP) into keys_out[0..m); vals likewise.  All
+// threads of the block must call it.  keys_in may equal keys_out.
 template <typename K, bool VALS, int THREADS, int IPT>
-struct BlockSortSmem : BlockSortScratch<K, VALS, THREADS, IPT> {
-    K keys[THREADS * IPT];
-    uint32_t vals[VALS ? THREADS * IPT : 1];
-};
-
-// Sort the m keys (m <= THREADS * IPT) a block holds in registers, warp-
-// striped (item i of lane l of warp w is key w * 32 * IPT + 32 i + l), with
-// their payload; on return the registers hold the sorted sequence in the same
-// arrangement.  skeys / svals: CAP-element staging arrays in shared memory
-// (may alias the buffer the keys were loaded from: every thread has read its
-// keys before the first write).  All threads of the block must call it.
-template <typename K, bool VALS, int THREADS, int IPT>
-__device__ __forceinline__ void block_sort_regs(K (&key)[IPT], uint32_t (&val)[IPT], uint32_t m,
-                                                K flip, BlockSortScratch<K, VALS, THREADS, IPT>& S,
-                                                K* skeys, uint32_t* svals) {
+__device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
+                                           const uint32_t* vals_in, uint32_t* vals_out,
+                                           uint32_t m, K flip,
+                                           BlockSortSmem<K, VALS, THREADS, IPT>& S) {
     constexpr int W = THREADS / 32;
     constexpr int WARP_ITEMS = 32 * IPT;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t wbase = warp * WARP_ITEMS;
 
+    K key[IPT];
+    uint32_t val[IPT];
     K lo = ~K(0), hi = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        if (wbase + 32 * i + lane < m) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) {
+            key[i] = keys_in[p];
+            if constexpr (VALS) val[i] = vals_in[p];
             const K o = key[i] ^ flip;
             lo = o < lo ? o : lo;
             hi = o > hi ? o : hi;
+        } else {
+            key[i] = 0;
+            if constexpr (VALS) val[i] = 0;
         }
     }
     // Block min / max of ord(x).
@@ -125,8 +125,8 @@ __device__ __forceinline__ void block_sort_regs(K (&key)[IPT], uint32_t (&val)[I
             if (d < (uint32_t)kBsRadix) {
                 const uint32_t lp = S.tile_start[d] + S.warp_hist[warp][d] + (dr[i] >> SH);
                 if (AHS_DCHECK(lp < m, "blocksort stage", lp)) {
-                    skeys[lp] = key[i];
-                    if constexpr (VALS) svals[lp] = val[i];
+                    S.keys[lp] = key[i];
+                    if constexpr (VALS) S.vals[lp] = val[i];
                 }
             }
         }
@@ -135,33 +135,12 @@ __device__ __forceinline__ void block_sort_regs(K (&key)[IPT], uint32_t (&val)[I
         for (int i = 0; i < IPT; ++i) {
             const uint32_t p = wbase + 32 * i + lane;
             if (p < m) {
-                key[i] = skeys[p];
-                if constexpr (VALS) val[i] = svals[p];
+                key[i] = S.keys[p];
+                if constexpr (VALS) val[i] = S.vals[p];
             }
         }
         __syncthreads();
     }
-}
-
-// Sort keys_in[0..m) (m <= CAP) into keys_out[0..m); vals likewise.  All
-// threads of the block must call it.  keys_in may equal keys_out.
-template <typename K, bool VALS, int THREADS, int IPT>
-__device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
-                                           const uint32_t* vals_in, uint32_t* vals_out,
-                                           uint32_t m, K flip,
-                                           BlockSortSmem<K, VALS, THREADS, IPT>& S) {
-    constexpr int WARP_ITEMS = 32 * IPT;
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t wbase = warp * WARP_ITEMS;
-    K key[IPT];
-    uint32_t val[IPT];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const uint32_t p = wbase + 32 * i + lane;
-        key[i] = p < m ? keys_in[p] : K(0);
-        if constexpr (VALS) val[i] = p < m ? vals_in[p] : 0u;
-    }
-    block_sort_regs<K, VALS, THREADS, IPT>(key, val, m, flip, S, S.keys, S.vals);
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         const uint32_t p = wbase + 32 * i + lane;

@@ -17,7 +17,8 @@ namespace ahs {
 namespace {
 
 constexpr int kK1Threads = 512;
-constexpr int kK1Unroll = 8;
+template <typename K>
+struct K1Unroll { static constexpr int kU = 4; };
 constexpr int kK2Unroll = 4;
 constexpr uint32_t kU32Bins = kHistSmemBytes / 4;           // bins that fit as u32 counters
 
@@ -47,16 +48,23 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
     if (gtid < n - tail0) k1_scalar(keys, tail0 + gtid, n, flip, mn, mx, desc);
 
     // Vector body; lanes of a warp hold consecutive vectors, so the pair that
-    // straddles two vectors is closed with a shuffle (lane 31 loads it).
+    // straddles two vectors is closed with a shuffle.  Lane 31 (and the owner
+    // of the last vector) needs the next vector's first key from memory: it is
+    // loaded together with the vectors so its latency overlaps theirs.
     const K* body = keys + head;
+    uint32_t dloc = 0;   // descents of this thread (fits 32 bits: < 2^32 keys per thread)
+    constexpr int kK1Unroll = K1Unroll<K>::kU;
     for (uint64_t wb = gtid - lane; wb < nvec; wb += stride * kK1Unroll) {
         Vec16<K> x[kK1Unroll];
+        K succ[kK1Unroll];
         bool ok[kK1Unroll];
 #pragma unroll
         for (int u = 0; u < kK1Unroll; ++u) {
             const uint64_t v = wb + lane + (uint64_t)u * stride;
             ok[u] = v < nvec;
             if (ok[u]) x[u] = load_vec16_stream(body + v * V);
+            const uint64_t e_next = head + (v + 1) * V;
+            succ[u] = (ok[u] && (lane == 31 || v + 1 == nvec) && e_next < n) ? keys[e_next] : K(0);
         }
 #pragma unroll
         for (int u = 0; u < kK1Unroll; ++u) {
@@ -72,15 +80,15 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
                     mx = o[j] > mx ? o[j] : mx;
                 }
 #pragma unroll
-                for (int j = 0; j + 1 < V; ++j) desc += (o[j] > o[j + 1]) ? 1ull : 0ull;
-                const uint64_t e_next = head + (v + 1) * V;
-                if (e_next < n) {
-                    const K on = (lane < 31 && v + 1 < nvec) ? nxt : (K)(keys[e_next] ^ flip);
-                    desc += (o[V - 1] > on) ? 1ull : 0ull;
+                for (int j = 0; j + 1 < V; ++j) dloc += (o[j] > o[j + 1]) ? 1u : 0u;
+                if (head + (v + 1) * V < n) {
+                    const K on = (lane < 31 && v + 1 < nvec) ? nxt : (K)(succ[u] ^ flip);
+                    dloc += (o[V - 1] > on) ? 1u : 0u;
                 }
             }
         }
     }
+    desc += dloc;
 
     // Block reduction.
     __shared__ unsigned long long s_min[kK1Threads / 32], s_max[kK1Threads / 32],
@@ -349,7 +357,7 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
 }  // namespace
 
 uint32_t k1_blocks(uint64_t n, int sms) {
-    const uint64_t per = (uint64_t)kK1Threads * kK1Unroll * 4;
+    const uint64_t per = (uint64_t)kK1Threads * 8 * 4;
     uint64_t b = ceil_div(n ? n : 1, per);
     const uint64_t cap = 2ull * (uint64_t)sms;   // two resident blocks per SM: one wave
     return (uint32_t)(b < cap ? b : cap);

@@ -462,17 +462,26 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
 
         // Bucket of each key and its slot in the tile's run of that bucket.
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
+        // A warp whose 32 keys share a bucket (runs of presorted input) takes
+        // its 32 slots with one atomic instead of 32 on the same counter.
+        const uint32_t lane = lane_id();
         K key[IPT];
         uint32_t br[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             const uint32_t p = i * kFastThreads + tid;
-            br[i] = kCols;
-            if (p < t.size) {
-                key[i] = buf[sp.pad + p];
-                const uint32_t b = cls((K)(key[i] ^ flip));
-                br[i] = (atomicAdd(&S.hist[b], 1u) << 10) | b;
+            key[i] = p < t.size ? buf[sp.pad + p] : K(0);
+            const uint32_t b = p < t.size ? cls((K)(key[i] ^ flip)) : kCols;
+            const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
+            uint32_t r;
+            if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
+                r = __shfl_sync(AHS_FULL_MASK, base, 0) + lane;
+            } else {
+                r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
             }
+            br[i] = (r << 10) | b;
         }
         __syncthreads();
 
@@ -497,7 +506,8 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
                 const uint32_t lp = S.tile_start[b] + (br[i] >> 10);
                 if (AHS_DCHECK(lp < t.size, "fast scatter stage", lp)) {
                     buf[lp] = key[i];
-                    S.bid[lp] = (uint16_t)b;
+                    // A digit is cheaper to recompute than to stage.
+                    if constexpr (MODE != kDigit) S.bid[lp] = (uint16_t)b;
                 }
             }
         }
@@ -506,9 +516,13 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         K* out = dst + sg.begin;
 #pragma unroll 4
         for (uint32_t j = tid; j < t.size; j += kFastThreads) {
-            const uint32_t gp = S.gbase[S.bid[j]] + j;
+            const K x = buf[j];
+            uint32_t b;
+            if constexpr (MODE == kDigit) b = cls((K)(x ^ flip));
+            else b = S.bid[j];
+            const uint32_t gp = S.gbase[b] + j;
             if (gp >= sg.size) { report_error(err, kDevBadState); continue; }
-            out[gp] = buf[j];
+            out[gp] = x;
         }
         __syncthreads();
         if (tid == 0) {
@@ -738,7 +752,7 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
     cudaError_t e = cudaMemcpyAsync(df, hf, nf * sizeof(FinalBucket), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
-                                 vtmp, vout, vin, vout, kd, st, ctx->sms, ctx->d_err);
+                                 vtmp, vout, vin, vout, kd, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
 }
@@ -1060,8 +1074,13 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
     if (binpos[nbins] != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
     // Keys of bin >= b are exactly those with ord(x) > thr(b).
     auto thr = [&](uint32_t b) { return (K)(mn + ((K)b << shift) - 1); };
+    // Partition `segs` (min_ord = first bin of the segment) at the given bin
+    // starts.  digit: every bucket is one bin and a segment spans <= 256 bins,
+    // so the bucket is the bin's offset from the segment's first bin -- the
+    // same splitters, classified without a search.
     auto run = [&](const K* src, K* dst, const std::vector<SegRange>& segs,
-                   const std::vector<std::vector<uint32_t>>& starts) -> ahs_status {
+                   const std::vector<std::vector<uint32_t>>& starts, bool digit) -> ahs_status {
+        if (segs.empty()) return AHS_OK;
         Level L;
         build_lists(segs, L, TK);
         std::vector<uint32_t> cur(segs.size() * kCols, 0);
@@ -1077,24 +1096,29 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
             }
             range_splitters<K>(t, spl.data() + q * 2 * kSlots);
         }
-        // min_ord carried the first bin for the host only; the classifier needs none.
-        for (SegDesc& sd : L.segs) sd.min_ord = 0;
-        ahs_status rc = upload_msd(ctx, L, cur, st, spl.data(), spl.size() * sizeof(K));
+        // The digit classifier takes the ord value of the segment's first bin.
+        for (SegDesc& sd : L.segs) sd.min_ord = digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift)) : 0ull;
+        ahs_status rc = digit ? upload_msd(ctx, L, cur, st)
+                              : upload_msd(ctx, L, cur, st, spl.data(), spl.size() * sizeof(K));
         if (rc != AHS_OK) return rc;
         const uint32_t nt = (uint32_t)L.tiles.size();
         const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
         uint64_t keys = 0;
         for (const SegRange& x : segs) keys += x.size;
         TraceScope ts("sample_scatter", keys, st);
-        ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-            src, dst, L.d_tiles, nt, L.d_segs, static_cast<const K*>(L.splitters), nullptr, flip, 0,
-            L.cursor, ctx->d_err);
+        if (digit)
+            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                src, dst, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift, L.cursor, ctx->d_err);
+        else
+            ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                src, dst, L.d_tiles, nt, L.d_segs, static_cast<const K*>(L.splitters), nullptr, flip,
+                0, L.cursor, ctx->d_err);
         return cuda_status(ctx, cudaGetLastError());
     };
 
     // Level 1: input -> temporary.
     const std::vector<uint32_t> s1 = group_bins(hist, 0, nbins, std::max<unsigned long long>(n / 256, 1));
-    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1});
+    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1}, false);
     if (rc != AHS_OK) return rc;
     // Level 2: every multi-bin run above a CTA's capacity, temporary -> output.
     std::vector<uint32_t> r1{0};
@@ -1123,7 +1147,19 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
     }
     uint32_t levels = 1;
     if (!segs2.empty()) {
-        rc = run(ktmp, kout, segs2, starts2);
+        // Segments whose buckets are single bins take the digit classifier.
+        std::vector<SegRange> sd, sr;
+        std::vector<std::vector<uint32_t>> td, tr;
+        for (size_t q = 0; q < segs2.size(); ++q) {
+            const uint32_t b0 = runs2[q].b0, b1 = runs2[q].b1;
+            const std::vector<uint32_t>& st_q = starts2[q];
+            bool single = (b1 - b0 <= 256) && st_q.size() == b1 - b0 - 1;
+            for (size_t j = 0; single && j < st_q.size(); ++j) single = st_q[j] == b0 + 1 + j;
+            (single ? sd : sr).push_back(segs2[q]);
+            (single ? td : tr).push_back(st_q);
+        }
+        rc = run(ktmp, kout, sd, td, true);
+        if (rc == AHS_OK) rc = run(ktmp, kout, sr, tr, false);
         if (rc != AHS_OK) return rc;
         levels = 2;
         for (size_t q = 0; q < segs2.size(); ++q) {

@@ -31,6 +31,6 @@ cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
                                  const uint64_t keys[kBucketClasses], const void* buf0, const void* buf1,
                                  const void* buf2, void* out, const uint32_t* vbuf0,
                                  const uint32_t* vbuf1, const uint32_t* vbuf2, uint32_t* vout,
-                                 KeyDesc kd, cudaStream_t st, int sms, uint32_t* err);
+                                 KeyDesc kd, cudaStream_t st);
 
 }  // namespace ahs
