@@ -35,7 +35,8 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
         "radix_digit_hist": w, "radix_onesweep": 2 * (w + v), "sample_count": w,
         "sample_scatter": 2 * (w + v), "bucket_sort_1k": 2 * (w + v), "bucket_sort_2k": 2 * (w + v),
         "segradix_count": w, "segradix_scatter": 2 * (w + v),
-        "bucket_sort_4k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
+        "bucket_sort_3k": 2 * (w + v), "bucket_sort_4k": 2 * (w + v),
+        "bucket_sort_6k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
         "blocksort_single": 2 * (w + v), "copy": 8,
         "msd_scatter": 2 * w, "msd_bin_minmax": w,
     }

@@ -22,8 +22,18 @@ blocksort_single(const K* keys_in, K* keys_out, const uint32_t* vals_in, uint32_
 // One CTA per final bucket: sort src[begin, begin+size) into out (sorted
 // buckets), or copy it (buckets whose keys are all equal need no pass).  The
 // source is buffer 0 (temporary), 1 (the output itself) or 2 (the input).
+// Resident CTAs per SM each keys-only uint32 bucket class is compiled for
+// (its registers then still hold the keys without spilling); wider keys and
+// payloads leave the register budget to the compiler.
+template <typename K, bool VALS, int T>
+struct BucketMinBlocks {
+    static constexpr int kN = (sizeof(K) == 4 && !VALS)
+                                  ? (T <= 128 ? 8 : (T <= 192 ? 5 : (T <= 256 ? 4 : 2)))
+                                  : 1;
+};
+
 template <typename K, bool VALS, int T, int IPT>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, BucketMinBlocks<K, VALS, T>::kN)
 bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1, const K* buf2,
               K* out, const uint32_t* vbuf0, const uint32_t* vbuf1, const uint32_t* vbuf2,
               uint32_t* vout, K flip) {
@@ -71,7 +81,13 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
                                          (int)sizeof(Smem));
     if (e != cudaSuccess) return e;
     // Grids are limited to 2^31 - 1 blocks in x; bucket lists are far smaller.
-    TraceScope ts(T * IPT <= 1024 ? "bucket_sort_1k" : (T * IPT <= 2048 ? "bucket_sort_2k" : (T * IPT <= 4096 ? "bucket_sort_4k" : "bucket_sort_8k")), keys, st);
+    constexpr int CAP = T * IPT;
+    TraceScope ts(CAP <= 1024 ? "bucket_sort_1k"
+                  : CAP <= 2048 ? "bucket_sort_2k"
+                  : CAP <= 3072 ? "bucket_sort_3k"
+                  : CAP <= 4096 ? "bucket_sort_4k"
+                  : CAP <= 6144 ? "bucket_sort_6k" : "bucket_sort_8k",
+                  keys, st);
     fn<<<count, T, sizeof(Smem), st>>>(d_list, static_cast<const K*>(b0), static_cast<const K*>(b1),
                                        static_cast<const K*>(b2), static_cast<K*>(out), vb0, vb1,
                                        vb2, vout, flip);
@@ -89,10 +105,16 @@ cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t 
         e = finish_class<K, VALS, 256, 8>(d_lists[1], counts[1], keys[1], b0, b1, b2, out, vb0,
                                           vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 256, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 192, 16>(d_lists[2], counts[2], keys[2], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 512, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 256, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
+                                           vb1, vb2, vout, flip, st);
+    if (e == cudaSuccess)
+        e = finish_class<K, VALS, 384, 16>(d_lists[4], counts[4], keys[4], b0, b1, b2, out, vb0,
+                                           vb1, vb2, vout, flip, st);
+    if (e == cudaSuccess)
+        e = finish_class<K, VALS, 512, 16>(d_lists[5], counts[5], keys[5], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     return e;
 }

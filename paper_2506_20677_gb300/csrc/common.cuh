@@ -150,36 +150,30 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* scratch, T* total) {
 }
 
 // Exclusive scan of NB per-digit counts with a block of BLOCK threads, for
-// any BLOCK (each thread owns NB / BLOCK consecutive digits when NB >= BLOCK).
-// start[d] = sum of count[d'] for d' < d.  Ends with __syncthreads, so start
-// is visible to the whole block on return.
+// any BLOCK: thread t owns the PER = ceil(NB / BLOCK) consecutive digits from
+// t * PER (threads past the end own none).  start[d] = sum of count[d'] for
+// d' < d.  Ends with __syncthreads, so start is visible to the whole block on
+// return.
 template <int BLOCK, int NB>
 __device__ __forceinline__ void scan_digit_counts(const uint32_t* count, uint32_t* start,
                                                   uint32_t* scratch) {
-    constexpr int PER = NB >= BLOCK ? NB / BLOCK : 1;
-    static_assert(NB < BLOCK || NB % BLOCK == 0, "digit count must divide evenly");
+    constexpr int PER = (NB + BLOCK - 1) / BLOCK;
     const uint32_t tid = threadIdx.x;
     uint32_t loc[PER];
     uint32_t sum = 0;
-    if constexpr (NB >= BLOCK) {
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            loc[r] = count[tid * PER + r];
-            sum += loc[r];
-        }
-    } else {
-        sum = tid < (uint32_t)NB ? count[tid] : 0u;
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t d = tid * PER + r;
+        loc[r] = d < (uint32_t)NB ? count[d] : 0u;
+        sum += loc[r];
     }
     uint32_t total;
     uint32_t run = block_exclusive_scan<BLOCK>(sum, scratch, &total);
-    if constexpr (NB >= BLOCK) {
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            start[tid * PER + r] = run;
-            run += loc[r];
-        }
-    } else {
-        if (tid < (uint32_t)NB) start[tid] = run;
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t d = tid * PER + r;
+        if (d < (uint32_t)NB) start[d] = run;
+        run += loc[r];
     }
     __syncthreads();
 }

@@ -908,16 +908,20 @@ void range_splitters(const std::vector<K>& thr, K* out) {
 }
 
 // Host: greedy grouping of bins [b0, b1) into at most 256 runs of about
-// `target` keys (a bin heavier than that is a run of its own).  Returns the
-// first bin of every run after the first.
+// `target` keys and at most `max_bins` bins (a bin heavier than the target
+// is a run of its own).  Returns the first bin of every run after the first.
 std::vector<uint32_t> group_bins(const std::vector<unsigned long long>& hist, uint32_t b0,
-                                 uint32_t b1, unsigned long long target) {
+                                 uint32_t b1, unsigned long long target,
+                                 uint32_t max_bins = 0xffffffffu) {
     std::vector<uint32_t> starts;
     unsigned long long acc = 0;
+    uint32_t first = b0;
     for (uint32_t b = b0; b < b1; ++b) {
-        if (acc > 0 && acc + hist[b] > target && starts.size() < kSlots - 1) {
+        if (b > first && (acc + hist[b] > target || b - first >= max_bins) &&
+            starts.size() < kSlots - 1) {
             starts.push_back(b);
             acc = 0;
+            first = b;
         }
         acc += hist[b];
     }
@@ -1079,7 +1083,8 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
     // so the bucket is the bin's offset from the segment's first bin -- the
     // same splitters, classified without a search.
     auto run = [&](const K* src, K* dst, const std::vector<SegRange>& segs,
-                   const std::vector<std::vector<uint32_t>>& starts, bool digit) -> ahs_status {
+                   const std::vector<std::vector<uint32_t>>& starts, bool digit,
+                   uint32_t dshift) -> ahs_status {
         if (segs.empty()) return AHS_OK;
         Level L;
         build_lists(segs, L, TK);
@@ -1108,7 +1113,7 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
         TraceScope ts("sample_scatter", keys, st);
         if (digit)
             ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                src, dst, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift, L.cursor, ctx->d_err);
+                src, dst, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, dshift, L.cursor, ctx->d_err);
         else
             ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
                 src, dst, L.d_tiles, nt, L.d_segs, static_cast<const K*>(L.splitters), nullptr, flip,
@@ -1116,9 +1121,21 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
         return cuda_status(ctx, cudaGetLastError());
     };
 
-    // Level 1: input -> temporary.
-    const std::vector<uint32_t> s1 = group_bins(hist, 0, nbins, std::max<unsigned long long>(n / 256, 1));
-    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1}, false);
+    // Level 1: input -> temporary.  When no block of 256 consecutive bins holds
+    // more than twice its share of the keys, the block boundaries are the
+    // splitters (classified by bit extraction); otherwise runs of bins of
+    // about n / 256 keys each.
+    const unsigned long long share = std::max<unsigned long long>((n + 255) / 256, 1);
+    std::vector<uint32_t> s1;
+    bool blocks = nbins > 256;
+    for (uint32_t c = 0; blocks && c * 256 < nbins; ++c)
+        blocks = binpos[std::min(nbins, (c + 1) * 256)] - binpos[c * 256] <= 2 * share;
+    if (blocks) {
+        for (uint32_t b = 256; b < nbins; b += 256) s1.push_back(b);
+    } else {
+        s1 = group_bins(hist, 0, nbins, share);
+    }
+    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1}, blocks, shift + 8);
     if (rc != AHS_OK) return rc;
     // Level 2: every multi-bin run above a CTA's capacity, temporary -> output.
     std::vector<uint32_t> r1{0};
@@ -1141,8 +1158,11 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
             if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
             continue;
         }
+        // Buckets span at most 16 bits of u (two 8-bit passes in shared memory).
         segs2.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
-        starts2.push_back(group_bins(hist, b0, b1, kBucketCap / 2));
+        const uint32_t span_bins = shift >= 16 ? 1u : 1u << (16 - shift);
+        starts2.push_back(group_bins(hist, b0, b1, kBucketCap / 2,
+                                     std::max<uint32_t>(span_bins, (b1 - b0 + 255) / 256)));
         runs2.push_back({b0, b1});
     }
     uint32_t levels = 1;
@@ -1158,8 +1178,8 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
             (single ? sd : sr).push_back(segs2[q]);
             (single ? td : tr).push_back(st_q);
         }
-        rc = run(ktmp, kout, sd, td, true);
-        if (rc == AHS_OK) rc = run(ktmp, kout, sr, tr, false);
+        rc = run(ktmp, kout, sd, td, true, shift);
+        if (rc == AHS_OK) rc = run(ktmp, kout, sr, tr, false, 0);
         if (rc != AHS_OK) return rc;
         levels = 2;
         for (size_t q = 0; q < segs2.size(); ++q) {

@@ -9,10 +9,11 @@
 namespace ahs {
 
 // Largest bucket one CTA sorts in shared memory, and the size classes of the
-// bucket kernels (128x8, 256x8, 256x16 and 512x16 threads x keys).
+// bucket kernels (threads x keys: 128x8, 256x8, 192x16, 256x16, 384x16,
+// 512x16).  Classes 1.5x apart keep a bucket's CTA at least two thirds full.
 constexpr uint32_t kBucketCap = 8192;
-constexpr int kBucketClasses = 4;
-constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 4096, 8192};
+constexpr int kBucketClasses = 6;
+constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 3072, 4096, 6144, 8192};
 
 // A bucket that leaves the partition levels: its keys sit in buffer `where`
 // (0: temporary, 1: the output, 2: the input) at [begin, begin + size).

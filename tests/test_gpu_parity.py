@@ -47,6 +47,19 @@ def _gen(kind, n, dt, seed):
         vals = rng.integers(info.min, info.max, size=64, dtype=dt, endpoint=True)
         p = 1.0 / np.arange(1, 65) ** 1.1
         return vals[rng.choice(64, size=n, p=p / p.sum())]
+    if kind == "clustered":
+        # 90% of the keys in a range narrower than one histogram bin (a heavy
+        # bin holding many values), the rest spread over the whole type.
+        lo = info.min // 2 + info.max // 2
+        c = lo + rng.integers(0, 4096, size=n).astype(dt)
+        wide = rng.integers(info.min, info.max, size=n, dtype=dt, endpoint=True)
+        return np.where(rng.random(n) < 0.9, c, wide).astype(dt)
+    if kind == "two_in_bin":
+        # Two heavy values inside one bin, plus a spread of others.
+        v0 = dt(info.max // 3)
+        pick = rng.random(n)
+        wide = rng.integers(info.min, info.max, size=n, dtype=dt, endpoint=True)
+        return np.where(pick < 0.45, v0, np.where(pick < 0.9, dt(v0 + 3), wide)).astype(dt)
     if kind == "all_equal":
         return np.full(n, dt(7), dtype=dt)
     if kind == "extremes":
@@ -68,7 +81,7 @@ def _check_features(f, of):
 DTS = [np.uint32, np.int32, np.uint64, np.int64]
 SIZES = [1, 2, 3, 17, 20, 21, 33, 1000, 8191, 8192, 8193, 65537, 300_001]
 KINDS = ["uniform_full", "small_range", "k65536", "zipf_wide", "all_equal", "extremes",
-         "sorted", "reversed"]
+         "sorted", "reversed", "clustered"]
 
 
 @pytest.mark.parametrize("dt", DTS, ids=lambda d: np.dtype(d).name)
@@ -117,7 +130,8 @@ def _sort_case(ahs, ctx, orc, a, force, kv, inplace=False):
 @pytest.mark.parametrize("dt", DTS, ids=lambda d: np.dtype(d).name)
 def test_forced_radix(ahs, ctx, orc, dt, kv):
     for i, n in enumerate(SIZES + [(1 << 20) + 5]):
-        for kind in ("uniform_full", "zipf_wide", "extremes", "k65536", "all_equal"):
+        for kind in ("uniform_full", "zipf_wide", "extremes", "k65536", "all_equal", "clustered",
+                     "two_in_bin"):
             r = _sort_case(ahs, ctx, orc, _gen(kind, n, dt, i), ahs.AHS_RADIX, kv)
             assert r.strategy == ahs.AHS_RADIX
 
@@ -126,7 +140,8 @@ def test_forced_radix(ahs, ctx, orc, dt, kv):
 @pytest.mark.parametrize("dt", DTS, ids=lambda d: np.dtype(d).name)
 def test_forced_general(ahs, ctx, orc, dt, kv):
     for i, n in enumerate(SIZES + [(1 << 21) + 9]):
-        for kind in ("uniform_full", "zipf_wide", "extremes", "sorted", "reversed", "all_equal"):
+        for kind in ("uniform_full", "zipf_wide", "extremes", "sorted", "reversed", "all_equal",
+                     "clustered", "two_in_bin"):
             _sort_case(ahs, ctx, orc, _gen(kind, n, dt, 7 + i), ahs.AHS_GENERAL, kv)
 
 
