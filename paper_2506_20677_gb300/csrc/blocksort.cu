@@ -28,7 +28,7 @@ blocksort_single(const K* keys_in, K* keys_out, const uint32_t* vals_in, uint32_
 template <typename K, bool VALS, int T>
 struct BucketMinBlocks {
     static constexpr int kN = (sizeof(K) == 4 && !VALS)
-                                  ? (T <= 128 ? 8 : (T <= 192 ? 5 : (T <= 256 ? 4 : 2)))
+                                  ? (T <= 128 ? 8 : (T <= 192 ? 5 : (T <= 256 ? 4 : (T <= 384 ? 3 : 2))))
                                   : 1;
 };
 
@@ -46,7 +46,7 @@ bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1
     K* dst = out + b.begin;
     uint32_t* vdst = VALS ? vout + b.begin : nullptr;
     if (b.sort) {
-        block_sort<K, VALS, T, IPT>(src, dst, vsrc, vdst, b.size, flip, S);
+        block_sort<K, VALS, T, IPT>(src, dst, vsrc, vdst, b.size, flip, S, (K)b.lo, b.bits);
     } else if (src != dst) {
         for (uint32_t i = threadIdx.x; i < b.size; i += T) {
             dst[i] = src[i];
@@ -123,11 +123,6 @@ cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t 
 
 uint64_t blocksort_capacity(uint32_t, bool) { return kBucketCap; }
 
-uint32_t bucket_class(uint32_t size) {
-    for (int c = 0; c < kBucketClasses - 1; ++c)
-        if (size <= kBucketClassCap[c]) return c;
-    return kBucketClasses - 1;
-}
 
 cudaError_t launch_blocksort_single(const void* keys_in, void* keys_out, const uint32_t* vals_in,
                                     uint32_t* vals_out, uint64_t n, KeyDesc kd, cudaStream_t st) {

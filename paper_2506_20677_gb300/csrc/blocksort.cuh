@@ -29,15 +29,21 @@ struct BlockSortSmem {
 
 // Sort keys_in[0..m) (m <= CAP) into keys_out[0..m); vals likewise.  All
 // threads of the block must call it.  keys_in may equal keys_out.
+// bits < 64: the caller guarantees lo_known <= ord(x) < lo_known + 2^bits for
+// every key, so the digits start from lo_known and no block-wide min / max
+// has to be waited for before the first pass (the pass count still shrinks
+// to what the keys' actual largest offset needs).
 template <typename K, bool VALS, int THREADS, int IPT>
 __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
                                            const uint32_t* vals_in, uint32_t* vals_out,
                                            uint32_t m, K flip,
-                                           BlockSortSmem<K, VALS, THREADS, IPT>& S) {
+                                           BlockSortSmem<K, VALS, THREADS, IPT>& S,
+                                           K lo_known = 0, uint32_t bits = 0xffu) {
     constexpr int W = THREADS / 32;
     constexpr int WARP_ITEMS = 32 * IPT;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t wbase = warp * WARP_ITEMS;
+    const bool known = bits < 64;
 
     K key[IPT];
     uint32_t val[IPT];
@@ -56,8 +62,16 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
             if constexpr (VALS) val[i] = 0;
         }
     }
-    // Block min / max of ord(x).
-    {
+    uint32_t passes;
+    if (known) {
+        // Warp maxima go to shared memory now; the first pass's barrier
+        // publishes them and the pass count is trimmed there.
+        lo = lo_known;
+        const unsigned long long b = warp_max((unsigned long long)hi);
+        if (lane == 0) S.red[1][warp] = b;
+        passes = (bits + 7) / 8;
+    } else {
+        // Block min / max of ord(x).
         unsigned long long a = warp_min((unsigned long long)lo), b = warp_max((unsigned long long)hi);
         if (lane == 0) { S.red[0][warp] = a; S.red[1][warp] = b; }
         __syncthreads();
@@ -71,9 +85,9 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
         lo = (K)a;
         hi = (K)b;
         __syncthreads();
+        const uint32_t D = m ? bitlen64((unsigned long long)(K)(hi - lo)) : 0;
+        passes = (D + 7) / 8;
     }
-    const uint32_t D = m ? bitlen64((unsigned long long)(K)(hi - lo)) : 0;
-    const uint32_t passes = (D + 7) / 8;
 
     if constexpr (kRankBlockSort == kRankAtomicOr) {
         for (uint32_t i = tid; i < W * kBsRadix; i += THREADS) (&S.warp_mask[0][0])[i] = 0;
@@ -82,6 +96,16 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
         const uint32_t shift = 8 * pass;
         for (uint32_t i = tid; i < W * kBsRadix; i += THREADS) (&S.warp_hist[0][0])[i] = 0;
         __syncthreads();
+        if (known && pass == 0) {
+            // Largest key of the block (warp maxima published by the barrier
+            // above): passes beyond the digits of its offset from lo are no-ops.
+            unsigned long long b = S.red[1][0];
+#pragma unroll
+            for (int w = 1; w < W; ++w) b = S.red[1][w] > b ? S.red[1][w] : b;
+            const uint32_t need = m ? (bitlen64((unsigned long long)(K)((K)b - lo)) + 7) / 8 : 0;
+            passes = need < passes ? need : passes;
+            if (passes == 0) break;
+        }
         uint32_t dr[IPT];
         {
             uint32_t dig[IPT];

@@ -722,7 +722,7 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
             // A large copy (an equality bucket of a heavy key) is split so
             // that many CTAs share it.
             for (uint32_t o = 0; o < f.size; o += kCopyChunk)
-                cls[0].push_back({f.begin + o, std::min(kCopyChunk, f.size - o), f.where, 0, 0});
+                cls[0].push_back(final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
             continue;
         }
         cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
@@ -770,10 +770,10 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
 
     std::vector<FinalBucket> finals;
     for (const SegRange& x : extra)
-        finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1 ? 1 : 0), 0});
+        finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
     std::vector<SegRange> open;
     for (const SegRange& x : segs) {
-        if (x.size <= kBucketCap) finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1), 0});
+        if (x.size <= kBucketCap) finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
         else open.push_back(x);
     }
     Level L;
@@ -811,9 +811,9 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
                 const unsigned long long b0 = L.segs[s].begin + base[(size_t)s * kCols + j];
                 const bool equal = (j & 1u) != 0;
                 if (equal || sz == 1) {
-                    if (where == 0) finals.push_back({b0, sz, where, 0, 0});   // copy to output
+                    if (where == 0) finals.push_back(final_bucket(b0, sz, where, false));   // copy to output
                 } else if (sz <= kBucketCap) {
-                    finals.push_back({b0, sz, where, 1, 0});
+                    finals.push_back(final_bucket(b0, sz, where, true));
                 } else {
                     next.push_back({b0, sz, 0});
                 }
@@ -855,15 +855,25 @@ ahs_status radix_segs_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin
     return AHS_OK;
 }
 
-// ------------------------------------------------------------ MSD radix (keys only)
+// ------------------------------------------------- keys-only histogram-guided partitions
 //
 // The feature pass leaves the exact histogram of the top 16 bits of
-// u = ord(x) - min (bin = u >> s, s = bitlen(span) - 16).  Two partition
-// passes by the bin's high and low byte -- whose bucket sizes are therefore
-// known without a counting pass -- leave every bin's keys at their final
-// position; a bin then holds keys that differ only in their low s bits and is
-// finished by the shared-memory sort (or, above its capacity, checked for a
-// single value and otherwise handed to the sample sort).
+// u = ord(x) - min (bin = u >> s, s = bitlen(span) - 16), so partition passes
+// whose bucket boundaries are bin boundaries know their bucket sizes without a
+// counting pass:
+//   RADIX (most significant digit first): pass 1 by the high byte of the bin,
+//     pass 2 by its low byte -- every bin's keys then sit at their final
+//     position, and a bin holds keys that differ only in their low s bits.
+//   GENERAL (sample sort with splitters from the histogram): level 1 splits at
+//     boundaries of 256-bin blocks when no block holds more than twice its
+//     share of the keys (classified by bit extraction), else at runs of bins
+//     of about n / 256 keys each (classified by splitter search); level 2 cuts
+//     each run into buckets spanning at most 16 bits of u.
+// Buckets that fit a CTA are sorted in shared memory; larger ones (bins heavier
+// than a CTA, with no finer information in the histogram) are checked for a
+// single value and otherwise sample-sorted.  All lists of a sort are built on
+// the host up front and uploaded in one copy, and the passes and bucket sorts
+// are launched back to back.
 
 // Upload segments, tiles and host-computed cursors of one pass into ctx->aux.
 ahs_status upload_msd(ahs_ctx* ctx, Level& L, const std::vector<uint32_t>& cursor, cudaStream_t st,
@@ -972,102 +982,50 @@ ahs_status finish_large(ahs_ctx* ctx, const std::vector<SegRange>& large, K* kou
     return rc;
 }
 
-template <typename K>
-ahs_status msd_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
-                 const std::vector<unsigned long long>& hist, uint32_t shift, void* scratch,
-                 cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
-    K* ktmp = static_cast<K*>(scratch);
-    cudaError_t e = set_attrs<K, false>();
-    if (e != cudaSuccess) return cuda_status(ctx, e);
-    constexpr uint32_t TK = FastCfg<K>::kTileKeys;
-    const uint32_t nbins = (uint32_t)hist.size();
-    ahs_status rc = AHS_OK;
-    const uint32_t nb1 = (nbins + 255) / 256;
-    std::vector<unsigned long long> t1(nb1, 0), base1(nb1, 0), binpos(nbins, 0);
-    unsigned long long run = 0;
-    for (uint32_t i = 0; i < nbins; ++i) {
-        binpos[i] = run;
-        run += hist[i];
-        t1[i >> 8] += hist[i];
-    }
-    if (run != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
-    for (uint32_t b = 0, r = 0; b < nb1; ++b) { base1[b] = r; r += (uint32_t)t1[b]; }
 
-    Level L;
-    // Pass 1: high byte of the bin, input -> temporary.
-    {
-        build_lists({SegRange{0ull, (uint32_t)n, (unsigned long long)mn}}, L, TK);
-        std::vector<uint32_t> cur(kCols, 0);
-        for (uint32_t b = 0; b < nb1; ++b) cur[b] = (uint32_t)base1[b];
-        rc = upload_msd(ctx, L, cur, st);
-        if (rc != AHS_OK) return rc;
-        const uint32_t nt = (uint32_t)L.tiles.size();
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
-        TraceScope ts("msd_scatter", n, st);
-        ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-            kin, ktmp, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift + 8, L.cursor,
-            ctx->d_err);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_status(ctx, e);
+// Arrays appended at 256-byte offsets into a window of the pinned staging
+// buffer, later copied in one piece to the same offsets of ctx->aux.
+struct Blob {
+    char* base;      // pinned host window
+    size_t cap;
+    size_t used = 0;
+    size_t add(const void* p, size_t bytes) {
+        const size_t off = used;
+        used += a256(bytes ? bytes : 1);
+        if (used > cap) return ~size_t(0);   // caller checks overflow()
+        if (bytes) std::memcpy(base + off, p, bytes);
+        return off;
     }
-    // Pass 2: low byte of the bin within each high-byte bucket, temporary -> output.
-    {
-        std::vector<SegRange> segs;
-        std::vector<uint32_t> which;
-        for (uint32_t b = 0; b < nb1; ++b) {
-            if (t1[b] == 0) continue;
-            segs.push_back({base1[b], (uint32_t)t1[b], (unsigned long long)mn});
-            which.push_back(b);
-        }
-        build_lists(segs, L, TK);
-        std::vector<uint32_t> cur(segs.size() * kCols, 0);
-        for (size_t q = 0; q < segs.size(); ++q) {
-            const uint32_t b = which[q];
-            for (uint32_t j = 0; j < 256 && b * 256 + j < nbins; ++j)
-                cur[q * kCols + j] = (uint32_t)(binpos[b * 256 + j] - base1[b]);
-        }
-        rc = upload_msd(ctx, L, cur, st);
-        if (rc != AHS_OK) return rc;
-        const uint32_t nt = (uint32_t)L.tiles.size();
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
-        TraceScope ts("msd_scatter", n, st);
-        ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-            ktmp, kout, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, shift, L.cursor,
-            ctx->d_err);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_status(ctx, e);
-    }
-    *levels_out = 2;
-    if (shift == 0) return AHS_OK;   // bins are single values: done
+    bool overflow() const { return used > cap; }
+};
 
-    // Bins: sort in shared memory, or (large) test for a single value first.
-    std::vector<FinalBucket> finals;
-    std::vector<SegRange> large;
-    for (uint32_t i = 0; i < nbins; ++i) {
-        if (hist[i] < 2) continue;
-        if (hist[i] <= kBucketCap) finals.push_back({binpos[i], (uint32_t)hist[i], 1, 1, 0});
-        else large.push_back({binpos[i], (uint32_t)hist[i], 0ull});
+// Final buckets sorted into the size classes of the bucket kernels; unsorted
+// (copy) buckets larger than kCopyChunk are split so that many CTAs share them.
+struct FinalPlan {
+    std::vector<FinalBucket> cls[kBucketClasses];
+    uint32_t sorted = 0;
+};
+FinalPlan plan_finals(const std::vector<FinalBucket>& finals) {
+    FinalPlan fp;
+    uint32_t per[kBucketClasses] = {};
+    for (const FinalBucket& f : finals) ++per[f.sort ? bucket_class(f.size) : 0];
+    for (int k = 0; k < kBucketClasses; ++k) fp.cls[k].reserve(per[k] + (k == 0 ? 64 : 0));
+    for (const FinalBucket& f : finals) {
+        if (!f.sort && f.size > kCopyChunk) {
+            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
+                fp.cls[0].push_back(final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
+            continue;
+        }
+        fp.cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
+        fp.sorted += f.sort;
     }
-    rc = finish_buckets(ctx, finals, ktmp, kout, kin, nullptr, nullptr, nullptr,
-                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
-    if (rc != AHS_OK || large.empty()) return rc;
-    return finish_large<K>(ctx, large, kout, n, flip, scratch, st, levels_out, buckets_out);
+    return fp;
 }
 
-// ------------------------------------------------------- general path, keys only
-//
-// The feature pass leaves the exact histogram of the top 16 bits of
-// u = ord(x) - min; its bin boundaries are splitters whose bucket sizes are
-// known exactly.  Level 1 cuts the bins into <= 256 runs of about n / 256 keys,
-// level 2 cuts every run into runs of about half a CTA's capacity, both with
-// the splitter classifier and no counting pass.  A bin heavier than its run
-// target is a bucket of its own; such buckets (no finer information in the
-// histogram) go on to sampled splitters.
 template <typename K>
-ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
-                          const std::vector<unsigned long long>& hist, uint32_t shift,
-                          void* scratch, cudaStream_t st, uint32_t* levels_out,
-                          uint32_t* buckets_out) {
+ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
+                       const std::vector<unsigned long long>& hist, uint32_t shift, bool msd,
+                       void* scratch, cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
     K* ktmp = static_cast<K*>(scratch);
     cudaError_t e = set_attrs<K, false>();
     if (e != cudaSuccess) return cuda_status(ctx, e);
@@ -1078,126 +1036,207 @@ ahs_status general_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K fli
     if (binpos[nbins] != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
     // Keys of bin >= b are exactly those with ord(x) > thr(b).
     auto thr = [&](uint32_t b) { return (K)(mn + ((K)b << shift) - 1); };
-    // Partition `segs` (min_ord = first bin of the segment) at the given bin
-    // starts.  digit: every bucket is one bin and a segment spans <= 256 bins,
-    // so the bucket is the bin's offset from the segment's first bin -- the
-    // same splitters, classified without a search.
-    auto run = [&](const K* src, K* dst, const std::vector<SegRange>& segs,
-                   const std::vector<std::vector<uint32_t>>& starts, bool digit,
-                   uint32_t dshift) -> ahs_status {
-        if (segs.empty()) return AHS_OK;
-        Level L;
-        build_lists(segs, L, TK);
-        std::vector<uint32_t> cur(segs.size() * kCols, 0);
-        std::vector<K> spl(segs.size() * 2 * kSlots);
-        for (size_t q = 0; q < segs.size(); ++q) {
-            std::vector<K> t;
-            const std::vector<uint32_t>& st_q = starts[q];
-            const uint32_t first = (uint32_t)(segs[q].min_ord);   // first bin of the segment
-            cur[q * kCols] = 0;
-            for (size_t j = 0; j < st_q.size(); ++j) {
-                t.push_back(thr(st_q[j]));
-                cur[q * kCols + j + 1] = (uint32_t)(binpos[st_q[j]] - binpos[first]);
-            }
-            range_splitters<K>(t, spl.data() + q * 2 * kSlots);
-        }
-        // The digit classifier takes the ord value of the segment's first bin.
-        for (SegDesc& sd : L.segs) sd.min_ord = digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift)) : 0ull;
-        ahs_status rc = digit ? upload_msd(ctx, L, cur, st)
-                              : upload_msd(ctx, L, cur, st, spl.data(), spl.size() * sizeof(K));
-        if (rc != AHS_OK) return rc;
-        const uint32_t nt = (uint32_t)L.tiles.size();
-        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
-        uint64_t keys = 0;
-        for (const SegRange& x : segs) keys += x.size;
-        TraceScope ts("sample_scatter", keys, st);
-        if (digit)
-            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                src, dst, L.d_tiles, nt, L.d_segs, nullptr, nullptr, flip, dshift, L.cursor, ctx->d_err);
-        else
-            ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                src, dst, L.d_tiles, nt, L.d_segs, static_cast<const K*>(L.splitters), nullptr, flip,
-                0, L.cursor, ctx->d_err);
-        return cuda_status(ctx, cudaGetLastError());
+    // Keys of bins [b0, b1) lie in [bin_lo(b0), bin_lo(b0) + 2^range_bits(b0, b1)).
+    auto bin_lo = [&](uint32_t b) { return (unsigned long long)(K)(mn + ((K)b << shift)); };
+    auto range_bits = [&](uint32_t b0, uint32_t b1) {
+        return bitlen64((((unsigned long long)(b1 - b0)) << shift) - 1);
     };
 
-    // Level 1: input -> temporary.  When no block of 256 consecutive bins holds
-    // more than twice its share of the keys, the block boundaries are the
-    // splitters (classified by bit extraction); otherwise runs of bins of
-    // about n / 256 keys each.
+    // Staging and device windows for the three uploads (level 1, level 2,
+    // final buckets), sized by upper bounds so that no upload has to wait for
+    // an earlier one: the host prepares level 2 while level 1 runs, and the
+    // bucket lists while level 2 runs.
+    const size_t max_tiles = n / TK + 2 * 256 + 2;
+    const size_t capA = a256(sizeof(SegDesc)) + a256((n / TK + 2) * sizeof(TileDesc)) +
+                        a256(kCols * 4) + a256(2 * kSlots * sizeof(K));
+    const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(max_tiles * sizeof(TileDesc)) +
+                             a256(256 * kCols * 4) + a256(256 * 2 * kSlots * sizeof(K)));
+    const size_t capC = kBucketClasses * a256((nbins + n / kCopyChunk + 8) * sizeof(FinalBucket));
+    ahs_status rc = ensure_aux(ctx, capA + capB + capC);
+    if (rc == AHS_OK) rc = ensure_stage(ctx, capA + capB + capC);
+    if (rc != AHS_OK) return rc;
+    char* aux = static_cast<char*>(ctx->aux);
+    char* stage = static_cast<char*>(ctx->h_stage);
+
+    // One partition pass: segments (min_ord carries the first bin), the bin
+    // starts of each segment's buckets after the first, and its classifier.
+    struct Pass {
+        std::vector<SegRange> segs;
+        std::vector<std::vector<uint32_t>> starts;
+        bool digit = false;
+        uint32_t dshift = 0;
+        const K* src = nullptr;
+        K* dst = nullptr;
+    };
+    // Lists of `P` into the blob, then its launch (after the blob's copy).
+    struct Placed {
+        size_t o_segs, o_tiles, o_cur, o_spl;
+        uint32_t nt;
+        uint64_t keys;
+    };
+    auto place = [&](const Pass& P, Blob& blob) -> Placed {
+        Level L;
+        build_lists(P.segs, L, TK);
+        std::vector<uint32_t> cur(P.segs.size() * kCols, 0);
+        std::vector<K> spl;
+        if (!P.digit) spl.resize(P.segs.size() * 2 * kSlots);
+        Placed pl{};
+        for (size_t q = 0; q < P.segs.size(); ++q) {
+            const uint32_t first = (uint32_t)P.segs[q].min_ord;   // first bin of the segment
+            std::vector<K> t;
+            for (size_t j = 0; j < P.starts[q].size(); ++j) {
+                const uint32_t b = P.starts[q][j];
+                if (!P.digit) t.push_back(thr(b));
+                cur[q * kCols + j + 1] = (uint32_t)(binpos[b] - binpos[first]);
+            }
+            if (!P.digit) range_splitters<K>(t, spl.data() + q * 2 * kSlots);
+            pl.keys += P.segs[q].size;
+        }
+        // The digit classifier takes the ord value of the segment's first bin.
+        for (SegDesc& sd : L.segs)
+            sd.min_ord = P.digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift)) : 0ull;
+        pl.o_segs = blob.add(L.segs.data(), L.segs.size() * sizeof(SegDesc));
+        pl.o_tiles = blob.add(L.tiles.data(), L.tiles.size() * sizeof(TileDesc));
+        pl.o_cur = blob.add(cur.data(), cur.size() * 4);
+        pl.o_spl = P.digit ? 0 : blob.add(spl.data(), spl.size() * sizeof(K));
+        pl.nt = (uint32_t)L.tiles.size();
+        return pl;
+    };
+    auto upload = [&](const Blob& blob, size_t window) -> cudaError_t {
+        return cudaMemcpyAsync(aux + window, stage + window, blob.used, cudaMemcpyHostToDevice, st);
+    };
+    auto launch = [&](const Pass& P, const Placed& pl, size_t window) -> cudaError_t {
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(pl.nt, 2ull * (uint64_t)ctx->sms);
+        const char* w = aux + window;
+        const SegDesc* d_segs = reinterpret_cast<const SegDesc*>(w + pl.o_segs);
+        const TileDesc* d_tiles = reinterpret_cast<const TileDesc*>(w + pl.o_tiles);
+        uint32_t* d_cur = reinterpret_cast<uint32_t*>(aux + window + pl.o_cur);
+        TraceScope ts(msd ? "msd_scatter" : "sample_scatter", pl.keys, st);
+        if (P.digit)
+            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, d_tiles, pl.nt, d_segs, nullptr, nullptr, flip, P.dshift, d_cur, ctx->d_err);
+        else
+            ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, d_tiles, pl.nt, d_segs, reinterpret_cast<const K*>(w + pl.o_spl), nullptr,
+                flip, 0, d_cur, ctx->d_err);
+        return cudaGetLastError();
+    };
+
+    // Level 1: input -> temporary.
     const unsigned long long share = std::max<unsigned long long>((n + 255) / 256, 1);
-    std::vector<uint32_t> s1;
     bool blocks = nbins > 256;
-    for (uint32_t c = 0; blocks && c * 256 < nbins; ++c)
+    for (uint32_t c = 0; !msd && blocks && c * 256 < nbins; ++c)
         blocks = binpos[std::min(nbins, (c + 1) * 256)] - binpos[c * 256] <= 2 * share;
+    std::vector<uint32_t> s1;
     if (blocks) {
         for (uint32_t b = 256; b < nbins; b += 256) s1.push_back(b);
     } else {
         s1 = group_bins(hist, 0, nbins, share);
     }
-    ahs_status rc = run(kin, ktmp, {SegRange{0ull, (uint32_t)n, 0ull}}, {s1}, blocks, shift + 8);
-    if (rc != AHS_OK) return rc;
-    // Level 2: every multi-bin run above a CTA's capacity, temporary -> output.
-    std::vector<uint32_t> r1{0};
-    r1.insert(r1.end(), s1.begin(), s1.end());
-    r1.push_back(nbins);
-    std::vector<SegRange> segs2;
-    std::vector<std::vector<uint32_t>> starts2;
+    {
+        Pass P1;
+        P1.segs.push_back({0ull, (uint32_t)n, 0ull});
+        P1.starts.push_back(s1);
+        P1.digit = blocks;
+        P1.dshift = shift + 8;
+        P1.src = kin;
+        P1.dst = ktmp;
+        Blob A{stage, capA};
+        const Placed pl = place(P1, A);
+        if (A.overflow()) return AHS_ERR_CUDA;
+        e = upload(A, 0);
+        if (e == cudaSuccess) e = launch(P1, pl, 0);
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+    }
+    *levels_out = 1;
+
+    // Level 2: every multi-bin run above a CTA's capacity, temporary -> output;
+    // runs that fit a CTA (and single heavy bins) leave here.
     std::vector<FinalBucket> finals;
+    finals.reserve(std::min<size_t>(nbins, n / 2 + 1));
     std::vector<SegRange> large;
-    struct Run { uint32_t b0, b1; };
-    std::vector<Run> runs2;
-    for (size_t g = 0; g + 1 < r1.size(); ++g) {
-        const uint32_t b0 = r1[g], b1 = r1[g + 1];
+    Pass Pd, Pr;
+    Pd.digit = true;
+    Pd.dshift = shift;
+    Pd.src = Pr.src = ktmp;
+    Pd.dst = Pr.dst = kout;
+    const uint32_t span_bins = msd || shift >= 16 ? 1u : 1u << (16 - shift);
+    for (size_t g = 0; g <= s1.size(); ++g) {
+        const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
         const unsigned long long sz = binpos[b1] - binpos[b0];
         if (sz == 0) continue;
         if (sz <= kBucketCap || b1 - b0 == 1) {
-            // Sorted (or, if large, first copied) from the temporary buffer.
-            const bool sort = sz <= kBucketCap && sz > 1;
-            finals.push_back({binpos[b0], (uint32_t)sz, 0, (uint8_t)sort, 0});
+            if (sz <= kBucketCap && sz > 1)
+                finals.push_back(final_bucket_bounded(binpos[b0], (uint32_t)sz, 0, bin_lo(b0), range_bits(b0, b1)));
+            else
+                finals.push_back(final_bucket(binpos[b0], (uint32_t)sz, 0, false));   // copy out
             if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
             continue;
         }
-        // Buckets span at most 16 bits of u (two 8-bit passes in shared memory).
-        segs2.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
-        const uint32_t span_bins = shift >= 16 ? 1u : 1u << (16 - shift);
-        starts2.push_back(group_bins(hist, b0, b1, kBucketCap / 2,
-                                     std::max<uint32_t>(span_bins, (b1 - b0 + 255) / 256)));
-        runs2.push_back({b0, b1});
-    }
-    uint32_t levels = 1;
-    if (!segs2.empty()) {
-        // Segments whose buckets are single bins take the digit classifier.
-        std::vector<SegRange> sd, sr;
-        std::vector<std::vector<uint32_t>> td, tr;
-        for (size_t q = 0; q < segs2.size(); ++q) {
-            const uint32_t b0 = runs2[q].b0, b1 = runs2[q].b1;
-            const std::vector<uint32_t>& st_q = starts2[q];
-            bool single = (b1 - b0 <= 256) && st_q.size() == b1 - b0 - 1;
-            for (size_t j = 0; single && j < st_q.size(); ++j) single = st_q[j] == b0 + 1 + j;
-            (single ? sd : sr).push_back(segs2[q]);
-            (single ? td : tr).push_back(st_q);
-        }
-        rc = run(ktmp, kout, sd, td, true, shift);
-        if (rc == AHS_OK) rc = run(ktmp, kout, sr, tr, false, 0);
-        if (rc != AHS_OK) return rc;
-        levels = 2;
-        for (size_t q = 0; q < segs2.size(); ++q) {
-            std::vector<uint32_t> r{runs2[q].b0};
-            r.insert(r.end(), starts2[q].begin(), starts2[q].end());
-            r.push_back(runs2[q].b1);
-            for (size_t j = 0; j + 1 < r.size(); ++j) {
-                const unsigned long long sz = binpos[r[j + 1]] - binpos[r[j]];
-                if (sz < 2) continue;
-                if (sz <= kBucketCap) finals.push_back({binpos[r[j]], (uint32_t)sz, 1, 1, 0});
-                else large.push_back({binpos[r[j]], (uint32_t)sz, 0ull});
+        std::vector<uint32_t> st2 = group_bins(hist, b0, b1, kBucketCap / 2,
+                                               std::max<uint32_t>(span_bins, (b1 - b0 + 255) / 256));
+        bool single = (b1 - b0 <= 256) && st2.size() == b1 - b0 - 1;
+        for (size_t j = 0; single && j < st2.size(); ++j) single = st2[j] == b0 + 1 + j;
+        // Sub-buckets of this run.
+        uint32_t lo_b = b0;
+        for (size_t j = 0; j <= st2.size(); ++j) {
+            const uint32_t hi_b = j == st2.size() ? b1 : st2[j];
+            const unsigned long long ssz = binpos[hi_b] - binpos[lo_b];
+            if (ssz >= 2) {
+                if (ssz <= kBucketCap)
+                    finals.push_back(final_bucket_bounded(binpos[lo_b], (uint32_t)ssz, 1, bin_lo(lo_b),
+                                                          range_bits(lo_b, hi_b)));
+                else
+                    large.push_back({binpos[lo_b], (uint32_t)ssz, 0ull});
             }
+            lo_b = hi_b;
+        }
+        Pass& P = single ? Pd : Pr;
+        P.segs.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
+        P.starts.push_back(std::move(st2));
+    }
+    {
+        Blob B{stage + capA, capB};
+        Placed pd{}, pr{};
+        if (!Pd.segs.empty()) pd = place(Pd, B);
+        if (!Pr.segs.empty()) pr = place(Pr, B);
+        if (B.overflow()) return AHS_ERR_CUDA;
+        if (B.used) {
+            e = upload(B, capA);
+            if (e == cudaSuccess && !Pd.segs.empty()) e = launch(Pd, pd, capA);
+            if (e == cudaSuccess && !Pr.segs.empty()) e = launch(Pr, pr, capA);
+            if (e != cudaSuccess) return cuda_status(ctx, e);
+            *levels_out = 2;
         }
     }
-    *levels_out = levels;
-    rc = finish_buckets(ctx, finals, ktmp, kout, kin, nullptr, nullptr, nullptr,
-                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
-    if (rc != AHS_OK) return rc;
+    // Final buckets.
+    const FinalPlan fp = plan_finals(finals);
+    {
+        Blob C{stage + capA + capB, capC};
+        size_t o_cls[kBucketClasses];
+        for (int k = 0; k < kBucketClasses; ++k)
+            o_cls[k] = C.add(fp.cls[k].data(), fp.cls[k].size() * sizeof(FinalBucket));
+        if (C.overflow()) return AHS_ERR_CUDA;
+        e = upload(C, capA + capB);
+        const FinalBucket* lists[kBucketClasses];
+        uint32_t counts[kBucketClasses];
+        uint64_t keys[kBucketClasses];
+        for (int k = 0; k < kBucketClasses; ++k) {
+            lists[k] = reinterpret_cast<const FinalBucket*>(aux + capA + capB + o_cls[k]);
+            counts[k] = (uint32_t)fp.cls[k].size();
+            keys[k] = 0;
+            for (const FinalBucket& f : fp.cls[k]) keys[k] += f.size;
+        }
+        if (e == cudaSuccess)
+            e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, kout, nullptr, nullptr,
+                                     nullptr, nullptr, KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st);
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+    }
+    *buckets_out = fp.sorted;
+    if (large.empty()) return AHS_OK;
+    // The pinned staging still feeds the copies above: wait before reusing it.
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
     return finish_large<K>(ctx, large, kout, n, flip, scratch, st, levels_out, buckets_out);
 }
 
@@ -1245,8 +1284,8 @@ ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const u
                               const std::vector<SegRange>& copy_segs, KeyDesc kd, cudaStream_t st) {
     std::vector<FinalBucket> finals;
     finals.reserve(sort_segs.size() + copy_segs.size());
-    for (const SegRange& x : sort_segs) finals.push_back({x.begin, x.size, 2, (uint8_t)(x.size > 1), 0});
-    for (const SegRange& x : copy_segs) finals.push_back({x.begin, x.size, 2, 0, 0});
+    for (const SegRange& x : sort_segs) finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
+    for (const SegRange& x : copy_segs) finals.push_back(final_bucket(x.begin, x.size, 2, false));
     // No temporary buffer is involved: every bucket reads kin and writes kout.
     return finish_buckets(ctx, finals, kout, kout, kin, vout, vout, vin, kd, st, nullptr);
 }
@@ -1259,11 +1298,11 @@ ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, 
     *buckets_out = 0;
     if (n > 0xffffffffull || hist.empty() || hist.size() > kMaxBins) return AHS_ERR_INVALID_ARG;
     if (kd.bytes == 4)
-        return msd_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n, (uint32_t)kd.flip,
-                               (uint32_t)min_ord, hist, shift, scratch, st, levels_out,
-                               buckets_out);
-    return msd_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip, min_ord, hist,
-                           shift, scratch, st, levels_out, buckets_out);
+        return keys_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n, (uint32_t)kd.flip,
+                                     (uint32_t)min_ord, hist, shift, true, scratch, st, levels_out,
+                                     buckets_out);
+    return keys_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip, min_ord,
+                                 hist, shift, true, scratch, st, levels_out, buckets_out);
 }
 
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
@@ -1279,11 +1318,11 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
     }
     if (!vin && hist && hist->size() > 256 && n <= 0xffffffffull) {
         if (kd.bytes == 4)
-            return general_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n,
-                                            (uint32_t)kd.flip, (uint32_t)min_ord, *hist, shift,
-                                            scratch, st, levels_out, buckets_out);
-        return general_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip,
-                                        min_ord, *hist, shift, scratch, st, levels_out, buckets_out);
+            return keys_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n,
+                                         (uint32_t)kd.flip, (uint32_t)min_ord, *hist, shift, false,
+                                         scratch, st, levels_out, buckets_out);
+        return keys_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip,
+                                     min_ord, *hist, shift, false, scratch, st, levels_out, buckets_out);
     }
     std::vector<SegRange> segs{{0ull, (uint32_t)n, 0ull}};
     return run_segmented_general(ctx, kin, kout, vin, vout, n, segs, {}, kd, scratch, st,

@@ -16,17 +16,34 @@ constexpr int kBucketClasses = 6;
 constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 3072, 4096, 6144, 8192};
 
 // A bucket that leaves the partition levels: its keys sit in buffer `where`
-// (0: temporary, 1: the output, 2: the input) at [begin, begin + size).
+// (0: temporary, 1: the output, 2: the input) at [begin, begin + size).  When
+// the partition fixed the bucket's range (bits != kBoundsUnknown), every key
+// has lo <= ord(x) < lo + 2^bits and the sort digits start from lo.
+constexpr uint8_t kBoundsUnknown = 0xff;
 struct FinalBucket {
     unsigned long long begin;
+    unsigned long long lo;
     uint32_t size;
     uint8_t where;
     uint8_t sort;      // 0: all keys equal (or one key), copy only
-    uint16_t pad;
+    uint8_t bits;
+    uint8_t pad;
 };
-static_assert(sizeof(FinalBucket) == 16, "FinalBucket layout");
+static_assert(sizeof(FinalBucket) == 24, "FinalBucket layout");
 
-uint32_t bucket_class(uint32_t size);
+inline FinalBucket final_bucket(unsigned long long begin, uint32_t size, uint8_t where, bool sort) {
+    return FinalBucket{begin, 0ull, size, where, (uint8_t)sort, kBoundsUnknown, 0};
+}
+inline FinalBucket final_bucket_bounded(unsigned long long begin, uint32_t size, uint8_t where,
+                                        unsigned long long lo, uint32_t bits) {
+    return FinalBucket{begin, lo, size, where, 1, (uint8_t)bits, 0};
+}
+
+inline uint32_t bucket_class(uint32_t size) {
+    for (int c = 0; c < kBucketClasses - 1; ++c)
+        if (size <= kBucketClassCap[c]) return c;
+    return kBucketClasses - 1;
+}
 cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
                                  const uint32_t counts[kBucketClasses],
                                  const uint64_t keys[kBucketClasses], const void* buf0, const void* buf1,
