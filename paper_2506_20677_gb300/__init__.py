@@ -275,6 +275,73 @@ class Context:
               "ahs_sort", self.handle)
         return SortResult(out, vals_out, info.strategy, info)
 
+    def sort_host(self, host_keys, host_out, key_type=None, force: int = AHS_AUTO,
+                  stream=None, device_buffers=None):
+        """Sort a sequence of host arrays (pinned, for asynchronous copies) into
+        the matching host outputs, overlapping the copy of array i + 1 to the
+        device and of array i - 1 back with the sort of array i.  Each array is
+        sorted on its own by ahs_sort.  device_buffers: optional pair of
+        (keys, out) device tensor pairs large enough for every array (reused
+        across calls).  Returns the strategies used."""
+        import torch
+        if len(host_out) != len(host_keys) or any(
+                h.dtype != host_keys[0].dtype or o.dtype != h.dtype or o.numel() != h.numel()
+                for h, o in zip(host_keys, host_out)):
+            raise AhsError(AHS_ERR_INVALID_ARG, "sort_host: one dtype, matching output sizes")
+        dev = torch.device("cuda", self.device)
+        cap = max((h.numel() for h in host_keys), default=0)
+        if device_buffers is None:
+            proto = host_keys[0] if host_keys else torch.empty(0, dtype=torch.int32)
+            device_buffers = [(torch.empty(cap, dtype=proto.dtype, device=dev),
+                               torch.empty(cap, dtype=proto.dtype, device=dev)) for _ in range(2)]
+        # Private streams for the sorts and both copy directions; the caller's
+        # stream orders them against its own work at entry and exit.
+        caller = stream if stream is not None else torch.cuda.current_stream(dev)
+        sort_st = torch.cuda.Stream(dev)
+        in_st = torch.cuda.Stream(dev)
+        out_st = torch.cuda.Stream(dev)
+        sort_st.wait_stream(caller)
+        in_st.wait_stream(caller)
+        out_st.wait_stream(caller)
+        loaded = [torch.cuda.Event() for _ in range(2)]
+        sorted_ev = [torch.cuda.Event() for _ in range(2)]
+        freed = [torch.cuda.Event() for _ in range(2)]     # buffer's output copied back
+        consumed = [torch.cuda.Event() for _ in range(2)]  # buffer's input read by the sort
+        picks = []
+
+        def load(i):
+            b = i % 2
+            with torch.cuda.stream(in_st):
+                if i >= 2:
+                    in_st.wait_event(consumed[b])
+                k = device_buffers[b][0][: host_keys[i].numel()]
+                k.copy_(host_keys[i], non_blocking=True)
+                loaded[b].record(in_st)
+
+        if host_keys:
+            load(0)
+        for i in range(len(host_keys)):
+            b = i % 2
+            if i + 1 < len(host_keys):
+                load(i + 1)
+            m = host_keys[i].numel()
+            k, o = device_buffers[b][0][:m], device_buffers[b][1][:m]
+            sort_st.wait_event(loaded[b])
+            if i >= 2:
+                sort_st.wait_event(freed[b])
+            r = self.sort(k, out=o, force=force, key_type=key_type, stream=sort_st)
+            consumed[b].record(sort_st)
+            sorted_ev[b].record(sort_st)
+            picks.append(r.strategy)
+            with torch.cuda.stream(out_st):
+                out_st.wait_event(sorted_ev[b])
+                host_out[i].copy_(o, non_blocking=True)
+                freed[b].record(out_st)
+        caller.wait_stream(sort_st)
+        caller.wait_stream(out_st)
+        caller.wait_stream(in_st)
+        return picks
+
     def sort_batch(self, keys, seg_offsets, out=None, vals=None, vals_out=None, key_type=None,
                    stream=None):
         import torch

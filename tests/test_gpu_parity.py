@@ -232,3 +232,20 @@ def test_repeated_calls_reuse_context(ahs, ctx, orc):
         if first is None:
             first = out
         assert np.array_equal(out, first)
+
+
+def test_sort_host_pipeline(ahs, ctx):
+    """Host arrays through Context.sort_host (copies overlapped with sorts)."""
+    import torch
+    rng = np.random.default_rng(11)
+    sizes = [300_001, 1, 0, 70_000, (1 << 20) + 3, 5]
+    arrays = [rng.integers(0, 2**32, size=m, dtype=np.uint32) for m in sizes]
+    arrays[3] = rng.integers(0, 4000, size=sizes[3], dtype=np.uint32)
+    host_in = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in arrays]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    for _ in range(2):   # the second call reuses nothing from the first
+        picks = ctx.sort_host(host_in, host_out, key_type=ahs.AHS_U32)
+        torch.cuda.synchronize()
+        assert len(picks) == len(arrays)
+        for a, o in zip(arrays, host_out):
+            assert np.array_equal(o.numpy().view(np.uint32), np.sort(a))
