@@ -70,17 +70,27 @@ seg_minmax(const K* __restrict__ keys, const SegChunk* __restrict__ chunks, K fl
            SegFeat* __restrict__ feat) {
     const SegChunk c = chunks[blockIdx.x];
     K mn = ~K(0), mx = 0;
-    unsigned long long desc = 0;
-    for (uint32_t i = threadIdx.x; i < c.len; i += kMmThreads) {
+    uint32_t desc = 0;
+    const uint32_t lane = lane_id();
+    // Warp-contiguous rows: the successor of a lane's key is the next lane's,
+    // and lane 31 loads its own (usually a cache hit).
+    for (uint32_t r = threadIdx.x - lane; r < c.len; r += kMmThreads) {
+        const uint32_t i = r + lane;
+        const bool ok = i < c.len;
         const unsigned long long e = c.begin + i;
-        const K o = keys[e] ^ flip;
-        mn = o < mn ? o : mn;
-        mx = o > mx ? o : mx;
-        if (e + 1 < c.seg_end) desc += (o > (K)(keys[e + 1] ^ flip)) ? 1ull : 0ull;
+        const K o = ok ? (K)(keys[e] ^ flip) : K(0);
+        const K nx = __shfl_down_sync(AHS_FULL_MASK, o, 1);
+        const bool has_next = ok && e + 1 < c.seg_end;
+        const K succ = (lane == 31 || i + 1 >= c.len) && has_next ? (K)(keys[e + 1] ^ flip) : nx;
+        if (ok) {
+            mn = o < mn ? o : mn;
+            mx = o > mx ? o : mx;
+            if (has_next) desc += (o > succ) ? 1u : 0u;
+        }
     }
     __shared__ unsigned long long s[3][kMmThreads / 32];
     unsigned long long a = warp_min((unsigned long long)mn), b = warp_max((unsigned long long)mx),
-                       d = warp_sum(desc);
+                       d = warp_sum((unsigned long long)desc);
     if (lane_id() == 0) { s[0][threadIdx.x >> 5] = a; s[1][threadIdx.x >> 5] = b; s[2][threadIdx.x >> 5] = d; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -93,6 +103,23 @@ seg_minmax(const K* __restrict__ keys, const SegChunk* __restrict__ chunks, K fl
         atomicMax(&feat[c.seg].max_ord, b);
         if (d) atomicAdd(&feat[c.seg].descents, d);
     }
+}
+
+// Calls f(key) for keys[0..n): each thread keeps kSegUnroll strided loads in
+// flight, so one CTA alone can stream a segment at a useful rate.
+constexpr int kSegUnroll = 8;
+template <int T, typename K, typename F>
+__device__ __forceinline__ void for_each_key(const K* __restrict__ keys, uint32_t n, F&& f) {
+    constexpr uint32_t kStep = (uint32_t)T * kSegUnroll;
+    uint32_t base = 0;
+    for (; base + kStep <= n; base += kStep) {
+        K x[kSegUnroll];
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; ++u) x[u] = __ldg(keys + base + u * T + threadIdx.x);
+#pragma unroll
+        for (int u = 0; u < kSegUnroll; ++u) f(x[u]);
+    }
+    for (uint32_t i = base + threadIdx.x; i < n; i += T) f(keys[i]);
 }
 
 __device__ __forceinline__ void seg_bins(unsigned long long mn, unsigned long long mx, uint32_t* s,
@@ -113,6 +140,27 @@ __device__ __forceinline__ double block_sum_1024(double v, double* red) {
     return t;
 }
 
+// Entropy terms in fp64 cost far more than the counting on this GPU (its
+// fp64 rate is a small fraction of the fp32 rate), so every distinct bin
+// count is evaluated once: cc[c] collects how many bins (or keys) have count
+// c for c < kCcMax, and only rarer, larger counts are evaluated per bin.
+constexpr uint32_t kCcMax = 4096;
+
+__device__ __forceinline__ double plogp(uint32_t c, double inv) {
+    const double p = (double)c * inv;
+    return -p * log2(p);
+}
+
+// Sum over c of weight(c) * plogp(c) for the collected counts (all threads).
+__device__ __forceinline__ double cc_sum(const uint32_t* cc, double inv, bool per_key) {
+    double t = 0.0;
+    for (uint32_t c = threadIdx.x + 1; c < kCcMax; c += kHistT) {
+        const uint32_t w = cc[c];
+        if (w) t += (double)(per_key ? w / c : w) * plogp(c, inv);
+    }
+    return t;
+}
+
 // One CTA per segment of at most 65,535 keys: 16-bit counters, two per word.
 template <typename K>
 __global__ void __launch_bounds__(kHistT, 1)
@@ -120,26 +168,53 @@ seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
                SegFeat* __restrict__ feat) {
     extern __shared__ __align__(16) uint32_t cnt[];
     __shared__ double red[kHistT / 32];
+    __shared__ uint32_t cc[kCcMax];
     const HistSeg g = segs[blockIdx.x];
     const K mn = (K)feat[g.seg].min_ord;
     uint32_t s, nb;
     seg_bins(feat[g.seg].min_ord, feat[g.seg].max_ord, &s, &nb);
     const uint32_t words = (nb + 1) / 2;
-    for (uint32_t i = threadIdx.x; i < words; i += kHistT) cnt[i] = 0;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < g.size; i += kHistT) {
-        const uint32_t bin = (uint32_t)((K)((K)(keys[g.begin + i] ^ flip) - mn) >> s);
-        atomicAdd(&cnt[bin >> 1], 1u << (16 * (bin & 1)));
-    }
-    __syncthreads();
-    double term = 0.0;
     const double inv = 1.0 / (double)g.size;
-    for (uint32_t i = threadIdx.x; i < words; i += kHistT) {
-        const uint32_t w = cnt[i];
-        const uint32_t c0 = w & 0xffffu, c1 = w >> 16;
-        if (c0) { const double p = (double)c0 * inv; term -= p * log2(p); }
-        if (c1) { const double p = (double)c1 * inv; term -= p * log2(p); }
+    double term = 0.0;
+    const K* p = keys + g.begin;
+    for (uint32_t i = threadIdx.x; i < kCcMax; i += kHistT) cc[i] = 0;
+    const bool by_key = (uint64_t)g.size * 4 < nb;
+    if (by_key) {
+        // Far fewer keys than bins: touch only the keys' own counters (zero
+        // them, count), then every key adds one to cc[count of its bin]; a
+        // bin of count c is seen c times.
+        for_each_key<kHistT>(p, g.size, [&](K x) {
+            cnt[(uint32_t)((K)((K)(x ^ flip) - mn) >> s) >> 1] = 0;
+        });
+        __syncthreads();
+        for_each_key<kHistT>(p, g.size, [&](K x) {
+            const uint32_t bin = (uint32_t)((K)((K)(x ^ flip) - mn) >> s);
+            atomicAdd(&cnt[bin >> 1], 1u << (16 * (bin & 1)));
+        });
+        __syncthreads();
+        for_each_key<kHistT>(p, g.size, [&](K x) {
+            const uint32_t bin = (uint32_t)((K)((K)(x ^ flip) - mn) >> s);
+            const uint32_t c = (cnt[bin >> 1] >> (16 * (bin & 1))) & 0xffffu;
+            if (c < kCcMax) atomicAdd(&cc[c], 1u);
+            else term += plogp(c, inv) / (double)c;
+        });
+    } else {
+        for (uint32_t i = threadIdx.x; i < words; i += kHistT) cnt[i] = 0;
+        __syncthreads();
+        for_each_key<kHistT>(p, g.size, [&](K x) {
+            const uint32_t bin = (uint32_t)((K)((K)(x ^ flip) - mn) >> s);
+            atomicAdd(&cnt[bin >> 1], 1u << (16 * (bin & 1)));
+        });
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < words; i += kHistT) {
+            const uint32_t w = cnt[i];
+            const uint32_t c0 = w & 0xffffu, c1 = w >> 16;
+            if (c0) { if (c0 < kCcMax) atomicAdd(&cc[c0], 1u); else term += plogp(c0, inv); }
+            if (c1) { if (c1 < kCcMax) atomicAdd(&cc[c1], 1u); else term += plogp(c1, inv); }
+        }
     }
+    __syncthreads();
+    term += cc_sum(cc, inv, by_key);
     const double t = block_sum_1024(term, red);
     if (threadIdx.x == 0) feat[g.seg].ent[0] = t;
 }
@@ -152,6 +227,7 @@ seg_hist_large(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
                SegFeat* __restrict__ feat) {
     extern __shared__ __align__(16) uint32_t cnt[];
     __shared__ double red[kHistT / 32];
+    __shared__ uint32_t cc[kCcMax];
     const uint32_t h = blockIdx.x & 1u;
     const HistSeg g = segs[blockIdx.x >> 1];
     const K mn = (K)feat[g.seg].min_ord;
@@ -161,19 +237,21 @@ seg_hist_large(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
     const uint32_t lo = h * half;
     const uint32_t len = h ? nb - half : half;
     for (uint32_t i = threadIdx.x; i < len; i += kHistT) cnt[i] = 0;
+    for (uint32_t i = threadIdx.x; i < kCcMax; i += kHistT) cc[i] = 0;
     __syncthreads();
-    const K* p = keys + g.begin;
-    for (uint32_t i = threadIdx.x; i < g.size; i += kHistT) {
-        const uint32_t b = (uint32_t)((K)((K)(p[i] ^ flip) - mn) >> s) - lo;
+    for_each_key<kHistT>(keys + g.begin, g.size, [&](K x) {
+        const uint32_t b = (uint32_t)((K)((K)(x ^ flip) - mn) >> s) - lo;
         if (b < len) atomicAdd(&cnt[b], 1u);
-    }
+    });
     __syncthreads();
     double term = 0.0;
     const double inv = 1.0 / (double)g.size;
     for (uint32_t i = threadIdx.x; i < len; i += kHistT) {
         const uint32_t c = cnt[i];
-        if (c) { const double q = (double)c * inv; term -= q * log2(q); }
+        if (c) { if (c < kCcMax) atomicAdd(&cc[c], 1u); else term += plogp(c, inv); }
     }
+    __syncthreads();
+    term += cc_sum(cc, inv, false);
     const double t = block_sum_1024(term, red);
     if (threadIdx.x == 0) feat[g.seg].ent[h] = t;
 }
@@ -200,9 +278,9 @@ seg_counting(const K* __restrict__ keys, K* __restrict__ out, const CountSeg* __
     const K mn = (K)g.min_ord;
     for (uint32_t i = threadIdx.x; i <= g.nb; i += kHistT) cnt[i] = 0;
     __syncthreads();
-    const K* p = keys + g.begin;
-    for (uint32_t i = threadIdx.x; i < g.size; i += kHistT)
-        atomicAdd(&cnt[(uint32_t)((K)(p[i] ^ flip) - mn)], 1u);
+    for_each_key<kHistT>(keys + g.begin, g.size, [&](K x) {
+        atomicAdd(&cnt[(uint32_t)((K)(x ^ flip) - mn)], 1u);
+    });
     __syncthreads();
     // Exclusive prefix over nb bins (each thread a contiguous run of bins).
     const uint32_t per = (g.nb + kHistT - 1) / kHistT;
@@ -284,17 +362,25 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
     std::memcpy(hsb + b_chunks + b_hs, hlarge.data(), hlarge.size() * sizeof(HistSeg));
     cudaError_t e = cudaMemcpyAsync(d_chunks, hsb, b_chunks + b_hs + b_hl, cudaMemcpyHostToDevice, st);
     const auto t0 = clock::now();
+    uint64_t keys_small = 0, keys_large = 0;
+    for (const HistSeg& h : hsmall) keys_small += h.size;
+    for (const HistSeg& h : hlarge) keys_large += h.size;
     if (e == cudaSuccess) {
-        TraceScope ts("batch_features", N, st);
-        seg_init<<<(n_seg + 255) / 256, 256, 0, st>>>(d_feat, n_seg);
-        if (!chunks.empty())
-            seg_minmax<K><<<(uint32_t)chunks.size(), kMmThreads, 0, st>>>(kin, d_chunks, flip, d_feat);
+        {
+            TraceScope ts("batch_minmax", N, st);
+            seg_init<<<(n_seg + 255) / 256, 256, 0, st>>>(d_feat, n_seg);
+            if (!chunks.empty())
+                seg_minmax<K><<<(uint32_t)chunks.size(), kMmThreads, 0, st>>>(kin, d_chunks, flip, d_feat);
+        }
         e = cudaFuncSetAttribute(seg_hist_small<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSegHistSmem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(seg_hist_large<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSegHistSmem);
-        if (e == cudaSuccess && !hsmall.empty())
+        if (e == cudaSuccess && !hsmall.empty()) {
+            TraceScope ts("batch_hist_small", keys_small, st);
             seg_hist_small<K><<<(uint32_t)hsmall.size(), kHistT, kSegHistSmem, st>>>(kin, d_hs, flip, d_feat);
+        }
         if (e == cudaSuccess && !hlarge.empty()) {
+            TraceScope ts("batch_hist_large", keys_large, st);
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2 * (uint32_t)hlarge.size());
             cfg.blockDim = dim3(kHistT);
@@ -346,8 +432,15 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
         case AHS_SMALL: small.push_back(r); break;
         case AHS_COUNTING: counting.push_back({b, (uint32_t)n, (uint32_t)(f.span + 1), r.min_ord}); break;
         case AHS_RADIX:
-            if (n <= kBucketCap) small.push_back(r);
-            else {
+            if (n <= kBucketCap) {
+                small.push_back(r);
+            } else if (!payload) {
+                // Keys only: the low-entropy segments of this class settle
+                // their heavy keys in equality buckets of the sampled-splitter
+                // levels at once, where digit levels would re-scatter them up
+                // to four times; equal keys make the result the same.
+                general.push_back(r);
+            } else {
                 radix.push_back(r);
                 radix_passes = std::max(radix_passes, (bitlen64(f.span) + 7) / 8);
             }

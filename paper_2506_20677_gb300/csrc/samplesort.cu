@@ -114,9 +114,16 @@ struct Classifier {
     }
 };
 
-// One CTA per segment: draw kSamples keys at hashed positions, sort them in
-// shared memory, keep the distinct values among the 255 quantiles, pad with
-// the largest value and lay them out as an implicit search tree.
+// Splitters a segment of `size` keys takes: enough for buckets of about half
+// a CTA's capacity, at most 255 (the tree's size).
+__host__ __device__ __forceinline__ uint32_t split_count(uint64_t size) {
+    const uint64_t want = (size + kBucketCap / 2 - 1) / (kBucketCap / 2);
+    return (uint32_t)(want <= 2 ? 1 : (want - 1 > kMaxSplit ? kMaxSplit : want - 1));
+}
+
+// One CTA per segment: draw 32 keys per wanted splitter at hashed positions,
+// sort them in shared memory, keep the distinct values among the quantiles,
+// pad with the largest value and lay them out as an implicit search tree.
 template <typename K>
 __global__ void __launch_bounds__(kThreads)
 ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t level, K flip,
@@ -128,17 +135,19 @@ ss_sample(const K* __restrict__ src, const SegDesc* __restrict__ segs, uint32_t 
     const SegDesc sg = segs[blockIdx.x];
     const unsigned long long salt =
         ((unsigned long long)level << 48) ^ ((unsigned long long)blockIdx.x << 20);
-    for (uint32_t i = threadIdx.x; i < kSamples; i += kThreads) {
+    const uint32_t m = split_count(sg.size);
+    const uint32_t nsamp = (m + 1) * kOversample;
+    for (uint32_t i = threadIdx.x; i < nsamp; i += kThreads) {
         const unsigned long long h = mix64((salt + i + 1) * 0x9E3779B97F4A7C15ull);
         const unsigned long long pos = __umul64hi(h, (unsigned long long)sg.size);
         S.keys[i] = src[sg.begin + pos];
     }
     __syncthreads();
-    block_sort<K, false, kThreads, kIpt>(S.keys, S.keys, nullptr, nullptr, kSamples, flip, S);
+    block_sort<K, false, kThreads, kIpt>(S.keys, S.keys, nullptr, nullptr, nsamp, flip, S);
     __syncthreads();
     uint32_t keep = 0;
     K cand = 0;
-    if (threadIdx.x < kMaxSplit) {
+    if (threadIdx.x < m) {
         cand = S.keys[(threadIdx.x + 1) * kOversample - 1] ^ flip;
         keep = (threadIdx.x == 0 || cand != (K)(S.keys[threadIdx.x * kOversample - 1] ^ flip)) ? 1u : 0u;
     }
@@ -423,8 +432,9 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
     auto issue = [&](int s, uint32_t k) {   // thread 0
         if (k >= ntiles) { cp_async_commit(); return; }   // keep one group per issue
         const TileDesc t = tiles[k];
-        issue_run(S.buf[s], src + t.begin, t.size, &S.bar[s], MODE != kDigit ? kSpBytes : 0u);
-        if constexpr (MODE != kDigit)
+        constexpr bool kTree = MODE == kSplit || MODE == kRange;
+        issue_run(S.buf[s], src + t.begin, t.size, &S.bar[s], kTree ? kSpBytes : 0u);
+        if constexpr (kTree)
             bulk_load(S.sp[s], splitters + (size_t)t.seg * 2 * kSlots, kSpBytes, &S.bar[s]);
     };
     if (tid == 0) {
@@ -447,7 +457,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         const SegDesc sg = segs[t.seg];
         const TileSplit<K> sp(src + t.begin, t.size);
         K* buf = S.buf[s];
-        if constexpr (MODE != kDigit) {
+        if constexpr (MODE == kSplit || MODE == kRange) {
             cls.tree = S.sp[s];
             cls.sorted = S.sp[s] + kSlots;
             if constexpr (MODE == kSplit) cls.m = nsplit[t.seg];
@@ -507,7 +517,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
                 if (AHS_DCHECK(lp < t.size, "fast scatter stage", lp)) {
                     buf[lp] = key[i];
                     // A digit is cheaper to recompute than to stage.
-                    if constexpr (MODE != kDigit) S.bid[lp] = (uint16_t)b;
+                    if constexpr (MODE == kSplit || MODE == kRange) S.bid[lp] = (uint16_t)b;
                 }
             }
         }
@@ -757,6 +767,8 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
     return cuda_status(ctx, e);
 }
 
+// Partition levels by sampled splitters until every bucket fits a CTA, then
+// the bucket sorts.
 template <typename K, bool VALS>
 ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uint32_t* vout,
                      uint64_t n_total, const std::vector<SegRange>& segs,
@@ -805,7 +817,8 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
         const uint32_t* base = reinterpret_cast<const uint32_t*>(hs + bread);
         std::vector<SegRange> next;
         for (uint32_t s = 0; s < ns; ++s) {
-            for (uint32_t j = 0; j < kCols; ++j) {
+            const uint32_t cols = 2 * split_count(L.segs[s].size) + 1;   // buckets in use
+            for (uint32_t j = 0; j < cols; ++j) {
                 const uint32_t sz = tot[(size_t)s * kCols + j];
                 if (sz == 0) continue;
                 const unsigned long long b0 = L.segs[s].begin + base[(size_t)s * kCols + j];
