@@ -36,7 +36,7 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
         "sample_scatter": 2 * (w + v), "bucket_sort_1k": 2 * (w + v), "bucket_sort_2k": 2 * (w + v),
         "segradix_count": w, "segradix_scatter": 2 * (w + v),
         "bucket_sort_3k": 2 * (w + v), "bucket_sort_4k": 2 * (w + v),
-        "bucket_sort_6k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
+        "bucket_sort_4.5k": 2 * (w + v), "bucket_sort_6k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
         "blocksort_single": 2 * (w + v), "copy": 8,
         "msd_scatter": 2 * w, "msd_bin_minmax": w,
     }
@@ -305,7 +305,7 @@ def run_ours(args, world, rank, local):
         per_strategy[v] = {"strategy": picks[v], "ms_p50": round(p50, 4), "ms_p99": round(p99, 4),
                            "gkeys_s_p50": round(n / (p50 / 1e3) / 1e9, 3)}
     kt = collections.defaultdict(lambda: [0, 0.0, 0])
-    for name, items, ms in trace:
+    for name, items, ms, _ in trace:
         kt[name][0] += 1
         kt[name][1] += ms
         kt[name][2] += items
@@ -561,7 +561,7 @@ def run_case(args, local):
     peak, kind = measured_peaks()
     import collections
     kt_ = collections.defaultdict(lambda: [0, 0.0, 0])
-    for name, items, t in trace:
+    for name, items, t, _ in trace:
         kt_[name][0] += 1
         kt_[name][1] += t
         kt_[name][2] += items

@@ -165,12 +165,15 @@ ahs_status ahs_load_model(ahs_ctx* ctx, const char* path);
 /* ---------------------------------------------------------------- tracing */
 
 /* One traced kernel launch: the kernel's name (static string), the keys it
- * processed (0 where not meaningful) and its device time from CUDA events
- * recorded around it on the launching stream. */
+ * processed (0 where not meaningful), its device time from CUDA events
+ * recorded around it on the launching stream, and when it started, in ms
+ * after the start of the first launch of the same collect (the gaps between
+ * launches are host work and transfers). */
 typedef struct {
     const char* kernel;
     uint64_t items;
     float ms;
+    float start_ms;
 } ahs_trace_entry_t;
 
 /* Turn per-launch tracing of this ctx's calls on (1) or off (0). */

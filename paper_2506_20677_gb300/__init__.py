@@ -87,7 +87,8 @@ class ahs_serve_stats_t(ctypes.Structure):
 
 
 class ahs_trace_entry_t(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_char_p), ("items", ctypes.c_uint64), ("ms", ctypes.c_float)]
+    _fields_ = [("kernel", ctypes.c_char_p), ("items", ctypes.c_uint64), ("ms", ctypes.c_float),
+                ("start_ms", ctypes.c_float)]
 
 
 # Every symbol include/ahs.h declares, with (restype, argtypes).
@@ -235,13 +236,15 @@ class Context:
         check(lib.ahs_trace_enable(self.handle, int(on)), "ahs_trace_enable")
 
     def trace_collect(self):
-        """[(kernel, items, ms)] of the launches traced since the last collect."""
+        """[(kernel, items, ms, start_ms)] of the launches traced since the last
+        collect; start_ms is measured from the start of the first of them."""
         cnt = ctypes.c_uint32()
         cap = 1 << 16
         buf = (ahs_trace_entry_t * cap)()
         check(lib.ahs_trace_collect(self.handle, buf, cap, ctypes.byref(cnt)), "ahs_trace_collect",
               self.handle)
-        return [(buf[i].kernel.decode(), buf[i].items, buf[i].ms) for i in range(min(cnt.value, cap))]
+        return [(buf[i].kernel.decode(), buf[i].items, buf[i].ms, buf[i].start_ms)
+                for i in range(min(cnt.value, cap))]
 
     # ------------------------------------------------------------ features
     def features(self, keys, key_type=None, stream=None) -> ahs_features_t:

@@ -408,9 +408,11 @@ ahs_status ahs_trace_collect(ahs_ctx* ctx, ahs_trace_entry_t* out, uint32_t cap,
         if (k < cap) {
             out[k].kernel = r.name;
             out[k].items = r.items;
-            float ms = 0.f;
+            float ms = 0.f, start = 0.f;
             cudaEventElapsedTime(&ms, r.a, r.b);
+            cudaEventElapsedTime(&start, ctx->tracer.records.front().a, r.a);
             out[k].ms = ms;
+            out[k].start_ms = start;
         }
         ++k;
         ctx->tracer.pool.push_back(r.a);

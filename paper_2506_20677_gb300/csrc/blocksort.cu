@@ -15,8 +15,12 @@ __global__ void __launch_bounds__(T)
 blocksort_single(const K* keys_in, K* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                  uint32_t n, K flip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<BlockSortSmem<K, VALS, T, IPT>*>(smem_raw);
-    block_sort<K, VALS, T, IPT>(keys_in, keys_out, vals_in, vals_out, n, flip, S);
+    if constexpr (VALS) {
+        auto& S = *reinterpret_cast<BlockSortSmem<K, VALS, T, IPT>*>(smem_raw);
+        block_sort<K, VALS, T, IPT>(keys_in, keys_out, vals_in, vals_out, n, flip, S);
+    } else {
+        block_sort_keys<K, T, IPT>(keys_in, keys_out, n, flip, smem_raw);
+    }
 }
 
 // One CTA per final bucket: sort src[begin, begin+size) into out (sorted
@@ -38,7 +42,6 @@ bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1
               K* out, const uint32_t* vbuf0, const uint32_t* vbuf1, const uint32_t* vbuf2,
               uint32_t* vout, K flip) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<BlockSortSmem<K, VALS, T, IPT>*>(smem_raw);
     const FinalBucket b = list[blockIdx.x];
     const K* src = (b.where == 0 ? buf0 : (b.where == 1 ? buf1 : buf2)) + b.begin;
     const uint32_t* vsrc =
@@ -46,7 +49,12 @@ bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1
     K* dst = out + b.begin;
     uint32_t* vdst = VALS ? vout + b.begin : nullptr;
     if (b.sort) {
-        block_sort<K, VALS, T, IPT>(src, dst, vsrc, vdst, b.size, flip, S, (K)b.lo, b.bits);
+        if constexpr (VALS) {
+            auto& S = *reinterpret_cast<BlockSortSmem<K, VALS, T, IPT>*>(smem_raw);
+            block_sort<K, VALS, T, IPT>(src, dst, vsrc, vdst, b.size, flip, S, (K)b.lo, b.bits);
+        } else {
+            block_sort_keys<K, T, IPT>(src, dst, b.size, flip, smem_raw, (K)b.lo, b.bits);
+        }
     } else if (src != dst) {
         for (uint32_t i = threadIdx.x; i < b.size; i += T) {
             dst[i] = src[i];
@@ -58,13 +66,13 @@ bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1
 template <typename K, bool VALS, int T, int IPT>
 cudaError_t single_t(const void* kin, void* kout, const uint32_t* vin, uint32_t* vout, uint32_t n,
                      K flip, cudaStream_t st) {
-    using Smem = BlockSortSmem<K, VALS, T, IPT>;
+    constexpr size_t kSmem = block_sort_smem_bytes<K, VALS, T, IPT>();
     auto fn = blocksort_single<K, VALS, T, IPT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
+                                         (int)kSmem);
     if (e != cudaSuccess) return e;
     TraceScope ts("blocksort_single", n, st);
-    fn<<<1, T, sizeof(Smem), st>>>(static_cast<const K*>(kin), static_cast<K*>(kout), vin, vout, n,
+    fn<<<1, T, kSmem, st>>>(static_cast<const K*>(kin), static_cast<K*>(kout), vin, vout, n,
                                    flip);
     return cudaGetLastError();
 }
@@ -75,10 +83,10 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
                          const uint32_t* vb1, const uint32_t* vb2, uint32_t* vout, K flip,
                          cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    using Smem = BlockSortSmem<K, VALS, T, IPT>;
+    constexpr size_t kSmem = block_sort_smem_bytes<K, VALS, T, IPT>();
     auto fn = bucket_finish<K, VALS, T, IPT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
+                                         (int)kSmem);
     if (e != cudaSuccess) return e;
     // Grids are limited to 2^31 - 1 blocks in x; bucket lists are far smaller.
     constexpr int CAP = T * IPT;
@@ -86,9 +94,10 @@ cudaError_t finish_class(const FinalBucket* d_list, uint32_t count, uint64_t key
                   : CAP <= 2048 ? "bucket_sort_2k"
                   : CAP <= 3072 ? "bucket_sort_3k"
                   : CAP <= 4096 ? "bucket_sort_4k"
+                  : CAP <= 4608 ? "bucket_sort_4.5k"
                   : CAP <= 6144 ? "bucket_sort_6k" : "bucket_sort_8k",
                   keys, st);
-    fn<<<count, T, sizeof(Smem), st>>>(d_list, static_cast<const K*>(b0), static_cast<const K*>(b1),
+    fn<<<count, T, kSmem, st>>>(d_list, static_cast<const K*>(b0), static_cast<const K*>(b1),
                                        static_cast<const K*>(b2), static_cast<K*>(out), vb0, vb1,
                                        vb2, vout, flip);
     return cudaGetLastError();
@@ -111,10 +120,13 @@ cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t 
         e = finish_class<K, VALS, 256, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 384, 16>(d_lists[4], counts[4], keys[4], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 288, 16>(d_lists[4], counts[4], keys[4], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 512, 16>(d_lists[5], counts[5], keys[5], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 384, 16>(d_lists[5], counts[5], keys[5], b0, b1, b2, out, vb0,
+                                           vb1, vb2, vout, flip, st);
+    if (e == cudaSuccess)
+        e = finish_class<K, VALS, 512, 16>(d_lists[6], counts[6], keys[6], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     return e;
 }

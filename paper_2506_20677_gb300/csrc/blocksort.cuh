@@ -175,4 +175,190 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
     }
 }
 
+// ------------------------------------------------------------ keys only
+//
+// Without a payload equal keys need no order among themselves, so a bucket
+// can be sorted by one counting pass instead of LSD passes: count the keys by
+// the top DB bits of u = ord(x) - min (DB chosen so there is about one
+// counter per key), place each key at its counter's slot in shared memory,
+// then give each key its final place inside its sub-bucket by counting the
+// sub-bucket's keys that precede it (smaller, or equal and earlier).  This is
+// the counting sort of Section III-C over the leading bits with an
+// insertion-style rank for the rest.  A sub-bucket of more than
+// kCountRankMax keys with different offsets would make the rank quadratic;
+// such a bucket is sorted by block_sort's LSD passes instead.
+constexpr uint32_t kCountRankMax = 32;
+
+__host__ __device__ constexpr uint32_t pow2_at_least(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Counter index with one padding word per 32: a thread that scans a run of
+// consecutive counters then meets no bank conflict with its neighbours.
+__device__ __forceinline__ uint32_t cnt_pad(uint32_t i) { return i + (i >> 5); }
+
+template <typename K, int THREADS, int IPT>
+struct BlockCountSmem {
+    static constexpr int W = THREADS / 32;
+    static constexpr uint32_t CAP = THREADS * IPT;
+    static constexpr uint32_t NB = pow2_at_least(CAP);
+    uint32_t cnt[NB + NB / 32 + 1];   // counts, then run starts; [cnt_pad(nb)] = m
+    uint32_t scan[W + 1];
+    unsigned long long red[2][W];
+    K keys[CAP];
+};
+
+// Dynamic shared memory a bucket kernel needs: the keys-only sort can fall
+// back to block_sort in the same bytes.
+template <typename K, bool VALS, int THREADS, int IPT>
+constexpr size_t block_sort_smem_bytes() {
+    return VALS || sizeof(BlockSortSmem<K, VALS, THREADS, IPT>) > sizeof(BlockCountSmem<K, THREADS, IPT>)
+               ? sizeof(BlockSortSmem<K, VALS, THREADS, IPT>)
+               : sizeof(BlockCountSmem<K, THREADS, IPT>);
+}
+
+// block_sort as a separate call, so that its registers are not added to the
+// counting path's.
+template <typename K, int THREADS, int IPT>
+__device__ __noinline__ void block_sort_keys_lsd(const K* keys_in, K* keys_out, uint32_t m, K flip,
+                                                 unsigned char* smem, K lo_known, uint32_t bits) {
+    block_sort<K, false, THREADS, IPT>(keys_in, keys_out, nullptr, nullptr, m, flip,
+                                       *reinterpret_cast<BlockSortSmem<K, false, THREADS, IPT>*>(smem),
+                                       lo_known, bits);
+}
+
+// Sort keys_in[0..m) (m <= THREADS*IPT) into keys_out[0..m), keys only.
+// smem holds block_sort_smem_bytes<K, false, THREADS, IPT>() bytes.
+// keys_in may equal keys_out.  lo_known / bits are passed to block_sort
+// when it takes over.
+template <typename K, int THREADS, int IPT>
+__device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, uint32_t m, K flip,
+                                                unsigned char* smem, K lo_known = 0,
+                                                uint32_t bits = 0xffu) {
+    using CS = BlockCountSmem<K, THREADS, IPT>;
+    CS& S = *reinterpret_cast<CS*>(smem);
+    constexpr int W = THREADS / 32;
+    constexpr int WARP_ITEMS = 32 * IPT;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const uint32_t wbase = warp * WARP_ITEMS;
+
+    // 2^lgm >= m counters at most; zero them before the first barrier.
+    const uint32_t lgm = m > 1 ? bitlen64(m - 1) : 0u;
+    for (uint32_t i = tid; i < cnt_pad(1u << lgm); i += THREADS) S.cnt[i] = 0;
+
+    K key[IPT];
+    K lo = ~K(0), hi = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) {
+            key[i] = keys_in[p];
+            const K o = key[i] ^ flip;
+            lo = o < lo ? o : lo;
+            hi = o > hi ? o : hi;
+        } else {
+            key[i] = 0;
+        }
+    }
+    {
+        const unsigned long long a = warp_min((unsigned long long)lo), b = warp_max((unsigned long long)hi);
+        if (lane == 0) { S.red[0][warp] = a; S.red[1][warp] = b; }
+    }
+    __syncthreads();
+    {
+        unsigned long long a = S.red[0][0], b = S.red[1][0];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            a = S.red[0][w] < a ? S.red[0][w] : a;
+            b = S.red[1][w] > b ? S.red[1][w] : b;
+        }
+        lo = (K)a;
+        hi = (K)b;
+    }
+    const uint32_t D = m ? bitlen64((unsigned long long)(K)(hi - lo)) : 0u;
+    if (D == 0) {   // at most one distinct key (block-uniform)
+        if (keys_in != keys_out) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) {
+                const uint32_t p = wbase + 32 * i + lane;
+                if (p < m) keys_out[p] = key[i];
+            }
+        }
+        return;
+    }
+    const uint32_t DB = D < lgm ? D : lgm;   // lgm >= 1 here, since m >= 2
+    const uint32_t R = D - DB;
+    const uint32_t nb = 1u << DB;
+
+    // Each key's slot in its counter (< 2^16), two to a register.
+    static_assert(THREADS * IPT <= 65536 && IPT % 2 == 0, "slots are packed in 16 bits");
+    uint32_t slot[IPT / 2];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        uint32_t r = 0;
+        if (p < m) {
+            const uint32_t d = (uint32_t)((K)((key[i] ^ flip) - lo) >> R);
+            r = atomicAdd(&S.cnt[cnt_pad(d)], 1u);
+        }
+        if (i & 1) slot[i / 2] |= r << 16;
+        else slot[i / 2] = r;
+    }
+    __syncthreads();
+
+    // Exclusive scan of the nb counters: thread t owns a run of C of them.
+    const uint32_t C = (nb + THREADS - 1) / THREADS;
+    const uint32_t c0 = tid * C < nb ? tid * C : nb;
+    const uint32_t c1 = c0 + C < nb ? c0 + C : nb;
+    uint32_t sum = 0, mx = 0;
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t v = S.cnt[cnt_pad(c)];
+        sum += v;
+        mx = v > mx ? v : mx;
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan<THREADS>(sum, S.scan, &total);
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t v = S.cnt[cnt_pad(c)];
+        S.cnt[cnt_pad(c)] = run;
+        run += v;
+    }
+    if (tid == 0) S.cnt[cnt_pad(nb)] = m;
+    if (__syncthreads_or(R > 0 && mx > kCountRankMax)) {
+        // Every thread is past its reads of the counters: the bytes are free.
+        block_sort_keys_lsd<K, THREADS, IPT>(keys_in, keys_out, m, flip, smem, lo_known, bits);
+        return;
+    }
+
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) {
+            const uint32_t d = (uint32_t)((K)((key[i] ^ flip) - lo) >> R);
+            const uint32_t lp = S.cnt[cnt_pad(d)] + ((slot[i / 2] >> (16 * (i & 1))) & 0xffffu);
+            if (AHS_DCHECK(lp < m, "count sort stage", lp)) S.keys[lp] = key[i];
+        }
+    }
+    __syncthreads();
+    if (R == 0) {
+        // Each sub-bucket holds one value: the staged order is sorted.
+        for (uint32_t p = tid; p < m; p += THREADS) keys_out[p] = S.keys[p];
+        return;
+    }
+    for (uint32_t p = tid; p < m; p += THREADS) {
+        const K x = S.keys[p];
+        const K o = x ^ flip;
+        const uint32_t d = (uint32_t)((K)(o - lo) >> R);
+        const uint32_t b = S.cnt[cnt_pad(d)], e = S.cnt[cnt_pad(d + 1)];
+        uint32_t r = b;
+        for (uint32_t j = b; j < e; ++j) {
+            const K y = S.keys[j] ^ flip;
+            r += (y < o || (y == o && j < p)) ? 1u : 0u;
+        }
+        if (AHS_DCHECK(r < m, "count sort rank", r)) keys_out[r] = x;
+    }
+}
+
 }  // namespace ahs

@@ -9,11 +9,13 @@
 namespace ahs {
 
 // Largest bucket one CTA sorts in shared memory, and the size classes of the
-// bucket kernels (threads x keys: 128x8, 256x8, 192x16, 256x16, 384x16,
-// 512x16).  Classes 1.5x apart keep a bucket's CTA at least two thirds full.
+// bucket kernels (threads x keys: 128x8, 256x8, 192x16, 256x16, 288x16,
+// 384x16, 512x16).  Classes at most 1.5x apart keep a bucket's CTA at least
+// two thirds full; the 4,608 class catches histogram bins of just over
+// 4,096 keys (2^28 keys in 2^16 bins).
 constexpr uint32_t kBucketCap = 8192;
-constexpr int kBucketClasses = 6;
-constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 3072, 4096, 6144, 8192};
+constexpr int kBucketClasses = 7;
+constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 3072, 4096, 4608, 6144, 8192};
 
 // A bucket that leaves the partition levels: its keys sit in buffer `where`
 // (0: temporary, 1: the output, 2: the input) at [begin, begin + size).  When

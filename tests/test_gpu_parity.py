@@ -60,6 +60,18 @@ def _gen(kind, n, dt, seed):
         pick = rng.random(n)
         wide = rng.integers(info.min, info.max, size=n, dtype=dt, endpoint=True)
         return np.where(pick < 0.45, v0, np.where(pick < 0.9, dt(v0 + 3), wide)).astype(dt)
+    if kind == "dup_spread":
+        # About four copies of each of n/4 values spread over the whole type:
+        # equal keys share a sub-bucket of the keys-only bucket sort.
+        vals = rng.integers(info.min, info.max, size=max(n // 4, 1), dtype=dt, endpoint=True)
+        return vals[rng.integers(0, len(vals), size=n)]
+    if kind == "half_equal":
+        # Half the keys one value, the rest within 2^20 above it: one
+        # sub-bucket of the keys-only bucket sort holds far more keys than the
+        # comparison rank takes, so the bucket falls back to LSD passes.
+        v0 = dt(info.max // 2 + 1)
+        spread = (v0 + rng.integers(0, 1 << 20, size=n)).astype(dt)
+        return np.where(rng.random(n) < 0.5, v0, spread).astype(dt)
     if kind == "all_equal":
         return np.full(n, dt(7), dtype=dt)
     if kind == "extremes":
@@ -131,7 +143,7 @@ def _sort_case(ahs, ctx, orc, a, force, kv, inplace=False):
 def test_forced_radix(ahs, ctx, orc, dt, kv):
     for i, n in enumerate(SIZES + [(1 << 20) + 5]):
         for kind in ("uniform_full", "zipf_wide", "extremes", "k65536", "all_equal", "clustered",
-                     "two_in_bin"):
+                     "two_in_bin", "dup_spread"):
             r = _sort_case(ahs, ctx, orc, _gen(kind, n, dt, i), ahs.AHS_RADIX, kv)
             assert r.strategy == ahs.AHS_RADIX
 
@@ -141,7 +153,7 @@ def test_forced_radix(ahs, ctx, orc, dt, kv):
 def test_forced_general(ahs, ctx, orc, dt, kv):
     for i, n in enumerate(SIZES + [(1 << 21) + 9]):
         for kind in ("uniform_full", "zipf_wide", "extremes", "sorted", "reversed", "all_equal",
-                     "clustered", "two_in_bin"):
+                     "clustered", "two_in_bin", "dup_spread", "half_equal"):
             _sort_case(ahs, ctx, orc, _gen(kind, n, dt, 7 + i), ahs.AHS_GENERAL, kv)
 
 
@@ -165,7 +177,8 @@ def test_counting_range_refused(ahs, ctx):
 def test_forced_small(ahs, ctx, orc, dt, kv):
     cap = int(ahs.lib.ahs_small_capacity(key_type(np.zeros(1, dt)), int(kv)))
     for i, n in enumerate([1, 2, 5, 16, 20, 21, 31, 32, 33, 500, 1024, 1025, 4095, cap - 1, cap]):
-        for kind in ("uniform_full", "small_range", "extremes", "all_equal", "reversed"):
+        for kind in ("uniform_full", "small_range", "extremes", "all_equal", "reversed",
+                     "dup_spread", "half_equal"):
             _sort_case(ahs, ctx, orc, _gen(kind, n, dt, 50 + i), ahs.AHS_SMALL, kv)
     with pytest.raises(ahs.AhsError):
         ctx.sort(dev(_gen("uniform_full", cap + 1, dt, 0)), force=ahs.AHS_SMALL,
