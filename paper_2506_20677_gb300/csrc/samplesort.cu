@@ -57,7 +57,7 @@ struct SegDesc {
     uint32_t size;
     uint32_t first_chunk;
     uint32_t nchunks;
-    uint32_t pad;
+    uint32_t first_tile;   // index of the segment's first tile in the pass's tile order
     unsigned long long min_ord;
 };
 struct TileDesc {
@@ -393,7 +393,12 @@ ss_scatter(const K* __restrict__ src, K* __restrict__ dst, const uint32_t* __res
 // atomic on the bucket's cursor (no cross-tile prefix is needed); the tile is
 // staged in bucket order and written out in coalesced runs.
 constexpr int kFastThreads = 512;
+constexpr uint32_t kSegCache = 256;   // segments of a pass that derives its tiles
 static_assert(kFastThreads == (int)kCols, "one bucket column per thread");
+// Words per segment in the cursor array of a pass: 2 m + 1 <= kCols buckets
+// with equality buckets, 256 for the digit and range classifiers.
+template <int MODE>
+constexpr uint32_t cursor_stride() { return MODE == kSplit ? kCols : 256u; }
 
 template <typename K>
 struct FastCfg {
@@ -412,13 +417,32 @@ struct FastSmem {
     uint32_t tile_start[kCols];
     uint32_t gbase[kCols];
     uint32_t scan[kFastThreads / 32 + 1];
+    SegDesc seg[kSegCache];   // the pass's segments, when it has no tile list
+    TileDesc tile[2];         // the tile in buf[s]
     uint64_t bar[2];
 };
+
+// Tile k of a pass without a tile list: segment q owns tiles
+// [segs[q].first_tile, segs[q+1].first_tile), each of `tile_keys` keys but
+// its last.
+__device__ __forceinline__ TileDesc tile_of(const SegDesc* segs, uint32_t nsegs, uint32_t k,
+                                            uint32_t tile_keys) {
+    uint32_t lo = 0, hi = nsegs;   // last q with first_tile <= k
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (segs[mid].first_tile <= k) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t off = (k - segs[lo].first_tile) * tile_keys;
+    const uint32_t size = segs[lo].size;
+    return {segs[lo].begin + off, size - off < tile_keys ? size - off : tile_keys, lo};
+}
 
 template <typename K, int MODE>
 __global__ void __launch_bounds__(kFastThreads, 2)
 ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* __restrict__ tiles,
-                uint32_t ntiles, const SegDesc* __restrict__ segs, const K* __restrict__ splitters,
+                const SegDesc* __restrict__ segs, uint32_t nsegs, uint32_t ntiles,
+                const K* __restrict__ splitters,
                 const uint32_t* __restrict__ nsplit, K flip, uint32_t shift,
                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ err) {
     constexpr int IPT = FastCfg<K>::kIpt;
@@ -431,12 +455,17 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
     constexpr uint32_t kSpBytes = 2 * kSlots * (uint32_t)sizeof(K);
     auto issue = [&](int s, uint32_t k) {   // thread 0
         if (k >= ntiles) { cp_async_commit(); return; }   // keep one group per issue
-        const TileDesc t = tiles[k];
+        const TileDesc t = tiles ? tiles[k] : tile_of(S.seg, nsegs, k, TILE);
+        S.tile[s] = t;
         constexpr bool kTree = MODE == kSplit || MODE == kRange;
         issue_run(S.buf[s], src + t.begin, t.size, &S.bar[s], kTree ? kSpBytes : 0u);
         if constexpr (kTree)
             bulk_load(S.sp[s], splitters + (size_t)t.seg * 2 * kSlots, kSpBytes, &S.bar[s]);
     };
+    if (!tiles) {   // nsegs <= kSegCache (the host checks)
+        for (uint32_t q = tid; q < nsegs; q += kFastThreads) S.seg[q] = segs[q];
+        __syncthreads();
+    }
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
@@ -453,8 +482,12 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         const uint32_t k = blockIdx.x + it * G;
         if (k >= ntiles) break;
         const int s = it & 1;
-        const TileDesc t = tiles[k];
-        const SegDesc sg = segs[t.seg];
+        if (!mbar_wait(&S.bar[s], (parity >> s) & 1u)) report_error(err, kDevCopyTimeout);
+        parity ^= 1u << s;
+        if (tid == 0) cp_async_wait_prior();   // head and tail keys of this tile
+        __syncthreads();   // also publishes S.tile[s], written when the tile was issued
+        const TileDesc t = S.tile[s];
+        const SegDesc sg = tiles ? segs[t.seg] : S.seg[t.seg];
         const TileSplit<K> sp(src + t.begin, t.size);
         K* buf = S.buf[s];
         if constexpr (MODE == kSplit || MODE == kRange) {
@@ -465,10 +498,6 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             cls.mn = (K)sg.min_ord;
             cls.shift = shift;
         }
-        if (!mbar_wait(&S.bar[s], (parity >> s) & 1u)) report_error(err, kDevCopyTimeout);
-        parity ^= 1u << s;
-        if (tid == 0) cp_async_wait_prior();   // head and tail keys of this tile
-        __syncthreads();
 
         // Bucket of each key and its slot in the tile's run of that bucket.
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
@@ -500,7 +529,8 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             const uint32_t j = tid;   // kFastThreads == kCols
             const uint32_t c = S.hist[j];
             S.hist[j] = 0;
-            const uint32_t base = c ? atomicAdd(&cursor[(size_t)t.seg * kCols + j], c) : 0u;
+            // c == 0 for every column past the classifier's buckets.
+            const uint32_t base = c ? atomicAdd(&cursor[(size_t)t.seg * cursor_stride<MODE>() + j], c) : 0u;
             uint32_t total;
             const uint32_t ex = block_exclusive_scan<kFastThreads>(c, S.scan, &total);
             S.tile_start[j] = ex;
@@ -607,6 +637,7 @@ void build_lists(const std::vector<SegRange>& open, Level& L, uint32_t tile_keys
         sd.first_chunk = (uint32_t)L.chunks.size();
         const uint32_t nt = (uint32_t)ceil_div(sd.size, tile_keys);
         const uint32_t t0 = (uint32_t)L.tiles.size();
+        sd.first_tile = t0;
         for (uint32_t t = 0; t < nt; ++t) {
             const uint32_t off = t * tile_keys;
             L.tiles.push_back({sd.begin + off, std::min(tile_keys, sd.size - off), s});
@@ -684,7 +715,7 @@ cudaError_t partition(const Level& L, const K* src, K* dst, const uint32_t* vsrc
             const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)sms);
             TraceScope ts(MODE == kSplit ? "sample_scatter" : "segradix_scatter", keys, st);
             ss_scatter_keys<K, MODE><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                src, dst, L.d_tiles, nt, L.d_segs, spl, L.nsplit, flip, shift, L.cursor, err);
+                src, dst, L.d_tiles, L.d_segs, ns, nt, spl, L.nsplit, flip, shift, L.cursor, err);
         }
         return cudaGetLastError();
     }
@@ -1059,11 +1090,9 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     // final buckets), sized by upper bounds so that no upload has to wait for
     // an earlier one: the host prepares level 2 while level 1 runs, and the
     // bucket lists while level 2 runs.
-    const size_t max_tiles = n / TK + 2 * 256 + 2;
-    const size_t capA = a256(sizeof(SegDesc)) + a256((n / TK + 2) * sizeof(TileDesc)) +
-                        a256(kCols * 4) + a256(2 * kSlots * sizeof(K));
-    const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(max_tiles * sizeof(TileDesc)) +
-                             a256(256 * kCols * 4) + a256(256 * 2 * kSlots * sizeof(K)));
+    const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(2 * kSlots * sizeof(K));
+    const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(256 * kCols * 4) +
+                             a256(256 * 2 * kSlots * sizeof(K)));
     const size_t capC = kBucketClasses * a256((nbins + n / kCopyChunk + 8) * sizeof(FinalBucket));
     ahs_status rc = ensure_aux(ctx, capA + capB + capC);
     if (rc == AHS_OK) rc = ensure_stage(ctx, capA + capB + capC);
@@ -1083,14 +1112,25 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     };
     // Lists of `P` into the blob, then its launch (after the blob's copy).
     struct Placed {
-        size_t o_segs, o_tiles, o_cur, o_spl;
-        uint32_t nt;
+        size_t o_segs, o_cur, o_spl;
+        uint32_t ns, nt;
         uint64_t keys;
     };
     auto place = [&](const Pass& P, Blob& blob) -> Placed {
-        Level L;
-        build_lists(P.segs, L, TK);
-        std::vector<uint32_t> cur(P.segs.size() * kCols, 0);
+        // Segments with their first tile; the kernel derives the tiles.
+        std::vector<SegDesc> segs(P.segs.size());
+        uint32_t nt = 0;
+        for (size_t q = 0; q < P.segs.size(); ++q) {
+            SegDesc& sd = segs[q];
+            sd.begin = P.segs[q].begin;
+            sd.size = P.segs[q].size;
+            sd.min_ord = P.segs[q].min_ord;
+            sd.first_tile = nt;
+            nt += (uint32_t)ceil_div(sd.size, TK);
+        }
+        constexpr uint32_t CS = cursor_stride<kDigit>();
+        static_assert(CS == cursor_stride<kRange>(), "one cursor layout for both classifiers");
+        std::vector<uint32_t> cur(P.segs.size() * CS, 0);
         std::vector<K> spl;
         if (!P.digit) spl.resize(P.segs.size() * 2 * kSlots);
         Placed pl{};
@@ -1100,37 +1140,38 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             for (size_t j = 0; j < P.starts[q].size(); ++j) {
                 const uint32_t b = P.starts[q][j];
                 if (!P.digit) t.push_back(thr(b));
-                cur[q * kCols + j + 1] = (uint32_t)(binpos[b] - binpos[first]);
+                cur[q * CS + j + 1] = (uint32_t)(binpos[b] - binpos[first]);
             }
             if (!P.digit) range_splitters<K>(t, spl.data() + q * 2 * kSlots);
             pl.keys += P.segs[q].size;
         }
         // The digit classifier takes the ord value of the segment's first bin.
-        for (SegDesc& sd : L.segs)
+        for (SegDesc& sd : segs)
             sd.min_ord = P.digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift)) : 0ull;
-        pl.o_segs = blob.add(L.segs.data(), L.segs.size() * sizeof(SegDesc));
-        pl.o_tiles = blob.add(L.tiles.data(), L.tiles.size() * sizeof(TileDesc));
+        pl.o_segs = blob.add(segs.data(), segs.size() * sizeof(SegDesc));
         pl.o_cur = blob.add(cur.data(), cur.size() * 4);
         pl.o_spl = P.digit ? 0 : blob.add(spl.data(), spl.size() * sizeof(K));
-        pl.nt = (uint32_t)L.tiles.size();
+        pl.ns = (uint32_t)segs.size();
+        pl.nt = nt;
         return pl;
     };
     auto upload = [&](const Blob& blob, size_t window) -> cudaError_t {
         return cudaMemcpyAsync(aux + window, stage + window, blob.used, cudaMemcpyHostToDevice, st);
     };
     auto launch = [&](const Pass& P, const Placed& pl, size_t window) -> cudaError_t {
+        if (pl.ns > kSegCache) return cudaErrorInvalidValue;   // level-1 runs are at most 256
         const uint32_t grid = (uint32_t)std::min<uint64_t>(pl.nt, 2ull * (uint64_t)ctx->sms);
         const char* w = aux + window;
         const SegDesc* d_segs = reinterpret_cast<const SegDesc*>(w + pl.o_segs);
-        const TileDesc* d_tiles = reinterpret_cast<const TileDesc*>(w + pl.o_tiles);
         uint32_t* d_cur = reinterpret_cast<uint32_t*>(aux + window + pl.o_cur);
         TraceScope ts(msd ? "msd_scatter" : "sample_scatter", pl.keys, st);
         if (P.digit)
             ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, d_tiles, pl.nt, d_segs, nullptr, nullptr, flip, P.dshift, d_cur, ctx->d_err);
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
+                ctx->d_err);
         else
             ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, d_tiles, pl.nt, d_segs, reinterpret_cast<const K*>(w + pl.o_spl), nullptr,
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, reinterpret_cast<const K*>(w + pl.o_spl), nullptr,
                 flip, 0, d_cur, ctx->d_err);
         return cudaGetLastError();
     };
