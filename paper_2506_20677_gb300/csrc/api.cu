@@ -232,7 +232,7 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
             const size_t need = samplesort_scratch_bytes(n, kd.bytes, false);
             rc = ensure_workspace(ctx, freg + need);
             if (rc != AHS_OK) return rc;
-            return run_msd_radix(ctx, kin, kout, n, kd, min_ord, hist, f.hist_shift,
+            return run_msd_radix(ctx, kin, kout, n, kd, min_ord, hist, f.hist_shift, group_slots(f),
                                  static_cast<char*>(ctx->ws) + freg, st, passes, buckets);
         }
         const RadixPlan plan = radix_plan(f.span);
@@ -266,7 +266,7 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
         if (rc != AHS_OK) return rc;
         return run_samplesort(ctx, kin, kout, vin, vout, n, kd, static_cast<char*>(ctx->ws) + freg,
                               st, passes, buckets, use_hist ? &hist : nullptr, min_ord,
-                              f.hist_shift);
+                              f.hist_shift, group_slots(f));
     }
     default:
         return AHS_ERR_INVALID_ARG;

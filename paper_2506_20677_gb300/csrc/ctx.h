@@ -74,11 +74,13 @@ ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes);
 // Keys only, with `hist` (the host copy of the feature histogram, bins of
 // (ord(x) - min_ord) >> shift): the first two levels take their splitters from
 // the histogram's bin boundaries (exact bucket sizes, no counting pass).
+// group: group_slots() of the input, the levels whose partition passes take
+// warp-aggregated slots.
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
                           uint32_t* levels_out, uint32_t* buckets_out,
                           const std::vector<unsigned long long>* hist = nullptr,
-                          uint64_t min_ord = 0, uint32_t shift = 0);
+                          uint64_t min_ord = 0, uint32_t shift = 0, uint32_t group = 0);
 
 // Keys-only radix sort, most significant digit first: two partition passes by
 // the high and low byte of the feature histogram's bin (exact bucket sizes
@@ -86,7 +88,19 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
 // then per-bin shared-memory sorts.  scratch: samplesort_scratch_bytes().
 ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
                          uint64_t min_ord, const std::vector<unsigned long long>& hist,
-                         uint32_t shift, void* scratch, cudaStream_t st, uint32_t* levels_out,
-                         uint32_t* buckets_out);
+                         uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
+                         uint32_t* levels_out, uint32_t* buckets_out);
+
+// Levels of the histogram-guided partitions whose scatter aggregates the slot
+// atomics of lanes sharing lane 0's bucket (measured on GB300: it pays where
+// a warp often holds a large group on one bucket counter but not the whole
+// warp, and costs elsewhere).  Level 1: runs broken by displaced keys (few
+// descents); wholly ordered warps take the plain path's one-atomic case.
+// Level 2: a skewed histogram (normalised entropy below 0.9), whose heavy
+// keys crowd the buckets of a level-1 run.
+constexpr uint32_t kGroupLevel1 = 1, kGroupLevel2 = 2;
+inline uint32_t group_slots(const ahs_features_t& f) {
+    return (f.descents < f.n / 4 ? kGroupLevel1 : 0u) | (f.entropy_norm < 0.9 ? kGroupLevel2 : 0u);
+}
 
 }  // namespace ahs

@@ -438,7 +438,7 @@ __device__ __forceinline__ TileDesc tile_of(const SegDesc* segs, uint32_t nsegs,
     return {segs[lo].begin + off, size - off < tile_keys ? size - off : tile_keys, lo};
 }
 
-template <typename K, int MODE>
+template <typename K, int MODE, bool GROUP = false>
 __global__ void __launch_bounds__(kFastThreads, 2)
 ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* __restrict__ tiles,
                 const SegDesc* __restrict__ segs, uint32_t nsegs, uint32_t ntiles,
@@ -503,6 +503,10 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
         // A warp whose 32 keys share a bucket (runs of presorted input) takes
         // its 32 slots with one atomic instead of 32 on the same counter.
+        // GROUP (inputs with runs or frequent keys): likewise the lanes that
+        // share lane 0's bucket, when they are a quarter of the warp or more.
+        // Lane 0 holds the warp's first key, so a lane past the tile never
+        // leads a group of valid lanes.
         const uint32_t lane = lane_id();
         K key[IPT];
         uint32_t br[IPT];
@@ -512,13 +516,28 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             key[i] = p < t.size ? buf[sp.pad + p] : K(0);
             const uint32_t b = p < t.size ? cls((K)(key[i] ^ flip)) : kCols;
             const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
-            uint32_t r;
-            if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
-                uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
-                r = __shfl_sync(AHS_FULL_MASK, base, 0) + lane;
+            uint32_t r = 0;
+            if constexpr (GROUP) {
+                const uint32_t m0 = __ballot_sync(AHS_FULL_MASK, b == b0);
+                if (b0 < kCols && __popc(m0) >= 8) {
+                    if (b == b0) {
+                        uint32_t base = 0;
+                        if (lane == 0) base = atomicAdd(&S.hist[b0], (uint32_t)__popc(m0));
+                        r = __shfl_sync(m0, base, 0) + __popc(m0 & lanemask_lt());
+                    } else if (b < kCols) {
+                        r = atomicAdd(&S.hist[b], 1u);
+                    }
+                } else if (b < kCols) {
+                    r = atomicAdd(&S.hist[b], 1u);
+                }
             } else {
-                r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
+                if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
+                    r = __shfl_sync(AHS_FULL_MASK, base, 0) + lane;
+                } else {
+                    r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
+                }
             }
             br[i] = (r << 10) | b;
         }
@@ -747,6 +766,8 @@ cudaError_t set_attrs() {
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kSplit>, sizeof(FastSmem<K>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit>, sizeof(FastSmem<K>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kRange>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, true>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kRange, true>, sizeof(FastSmem<K>));
     return e;
 }
 
@@ -1069,7 +1090,8 @@ FinalPlan plan_finals(const std::vector<FinalBucket>& finals) {
 template <typename K>
 ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
                        const std::vector<unsigned long long>& hist, uint32_t shift, bool msd,
-                       void* scratch, cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
+                       uint32_t group, void* scratch, cudaStream_t st, uint32_t* levels_out,
+                       uint32_t* buckets_out) {
     K* ktmp = static_cast<K*>(scratch);
     cudaError_t e = set_attrs<K, false>();
     if (e != cudaSuccess) return cuda_status(ctx, e);
@@ -1106,6 +1128,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         std::vector<SegRange> segs;
         std::vector<std::vector<uint32_t>> starts;
         bool digit = false;
+        bool group = false;   // warp-aggregated slot atomics
         uint32_t dshift = 0;
         const K* src = nullptr;
         K* dst = nullptr;
@@ -1165,14 +1188,21 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         const SegDesc* d_segs = reinterpret_cast<const SegDesc*>(w + pl.o_segs);
         uint32_t* d_cur = reinterpret_cast<uint32_t*>(aux + window + pl.o_cur);
         TraceScope ts(msd ? "msd_scatter" : "sample_scatter", pl.keys, st);
-        if (P.digit)
+        const K* spl = reinterpret_cast<const K*>(w + pl.o_spl);
+        if (P.digit && P.group)
+            ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
+                ctx->d_err);
+        else if (P.digit)
             ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
                 P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
                 ctx->d_err);
+        else if (P.group)
+            ss_scatter_keys<K, kRange, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err);
         else
             ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, reinterpret_cast<const K*>(w + pl.o_spl), nullptr,
-                flip, 0, d_cur, ctx->d_err);
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err);
         return cudaGetLastError();
     };
 
@@ -1193,6 +1223,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         P1.starts.push_back(s1);
         P1.digit = blocks;
         P1.dshift = shift + 8;
+        P1.group = (group & kGroupLevel1) != 0;
         P1.src = kin;
         P1.dst = ktmp;
         Blob A{stage, capA};
@@ -1211,6 +1242,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     std::vector<SegRange> large;
     Pass Pd, Pr;
     Pd.digit = true;
+    Pd.group = Pr.group = (group & kGroupLevel2) != 0;
     Pd.dshift = shift;
     Pd.src = Pr.src = ktmp;
     Pd.dst = Pr.dst = kout;
@@ -1346,24 +1378,24 @@ ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const u
 
 ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
                          uint64_t min_ord, const std::vector<unsigned long long>& hist,
-                         uint32_t shift, void* scratch, cudaStream_t st, uint32_t* levels_out,
-                         uint32_t* buckets_out) {
+                         uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
+                         uint32_t* levels_out, uint32_t* buckets_out) {
     *levels_out = 0;
     *buckets_out = 0;
     if (n > 0xffffffffull || hist.empty() || hist.size() > kMaxBins) return AHS_ERR_INVALID_ARG;
     if (kd.bytes == 4)
         return keys_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n, (uint32_t)kd.flip,
-                                     (uint32_t)min_ord, hist, shift, true, scratch, st, levels_out,
-                                     buckets_out);
+                                     (uint32_t)min_ord, hist, shift, true, group, scratch, st,
+                                     levels_out, buckets_out);
     return keys_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip, min_ord,
-                                 hist, shift, true, scratch, st, levels_out, buckets_out);
+                                 hist, shift, true, group, scratch, st, levels_out, buckets_out);
 }
 
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
                           uint32_t* levels_out, uint32_t* buckets_out,
                           const std::vector<unsigned long long>* hist, uint64_t min_ord,
-                          uint32_t shift) {
+                          uint32_t shift, uint32_t group) {
     *levels_out = 0;
     *buckets_out = 0;
     if (n <= kBucketCap) {
@@ -1374,9 +1406,10 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
         if (kd.bytes == 4)
             return keys_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n,
                                          (uint32_t)kd.flip, (uint32_t)min_ord, *hist, shift, false,
-                                         scratch, st, levels_out, buckets_out);
+                                         group, scratch, st, levels_out, buckets_out);
         return keys_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n, kd.flip,
-                                     min_ord, *hist, shift, false, scratch, st, levels_out, buckets_out);
+                                     min_ord, *hist, shift, false, group, scratch, st, levels_out,
+                                     buckets_out);
     }
     std::vector<SegRange> segs{{0ull, (uint32_t)n, 0ull}};
     return run_segmented_general(ctx, kin, kout, vin, vout, n, segs, {}, kd, scratch, st,
