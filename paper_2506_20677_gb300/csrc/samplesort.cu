@@ -1064,28 +1064,31 @@ struct Blob {
     bool overflow() const { return used > cap; }
 };
 
-// Final buckets sorted into the size classes of the bucket kernels; unsorted
-// (copy) buckets larger than kCopyChunk are split so that many CTAs share them.
-struct FinalPlan {
-    std::vector<FinalBucket> cls[kBucketClasses];
+// Final buckets written straight into the pinned staging, one region of
+// `cap` entries per size class of the bucket kernels; unsorted (copy) buckets
+// larger than kCopyChunk are split so that many CTAs share them.
+struct ClassLists {
+    FinalBucket* region[kBucketClasses];
+    size_t cap = 0;
+    uint32_t count[kBucketClasses] = {};
+    uint64_t keys[kBucketClasses] = {};
     uint32_t sorted = 0;
-};
-FinalPlan plan_finals(const std::vector<FinalBucket>& finals) {
-    FinalPlan fp;
-    uint32_t per[kBucketClasses] = {};
-    for (const FinalBucket& f : finals) ++per[f.sort ? bucket_class(f.size) : 0];
-    for (int k = 0; k < kBucketClasses; ++k) fp.cls[k].reserve(per[k] + (k == 0 ? 64 : 0));
-    for (const FinalBucket& f : finals) {
+    bool overflow = false;
+    void put(int k, const FinalBucket& f) {
+        if (count[k] >= cap) { overflow = true; return; }
+        region[k][count[k]++] = f;
+        keys[k] += f.size;
+    }
+    void add(const FinalBucket& f) {
         if (!f.sort && f.size > kCopyChunk) {
             for (uint32_t o = 0; o < f.size; o += kCopyChunk)
-                fp.cls[0].push_back(final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
-            continue;
+                put(0, final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
+            return;
         }
-        fp.cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
-        fp.sorted += f.sort;
+        put(f.sort ? (int)bucket_class(f.size) : 0, f);
+        sorted += f.sort;
     }
-    return fp;
-}
+};
 
 template <typename K>
 ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
@@ -1115,7 +1118,9 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(2 * kSlots * sizeof(K));
     const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(256 * kCols * 4) +
                              a256(256 * 2 * kSlots * sizeof(K)));
-    const size_t capC = kBucketClasses * a256((nbins + n / kCopyChunk + 8) * sizeof(FinalBucket));
+    const size_t class_cap = nbins + n / kCopyChunk + 8;   // entries of one class region
+    const size_t class_bytes = a256(class_cap * sizeof(FinalBucket));
+    const size_t capC = kBucketClasses * class_bytes;
     ahs_status rc = ensure_aux(ctx, capA + capB + capC);
     if (rc == AHS_OK) rc = ensure_stage(ctx, capA + capB + capC);
     if (rc != AHS_OK) return rc;
@@ -1236,9 +1241,9 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     *levels_out = 1;
 
     // Level 2: every multi-bin run above a CTA's capacity, temporary -> output;
-    // runs that fit a CTA (and single heavy bins) leave here.
-    std::vector<FinalBucket> finals;
-    finals.reserve(std::min<size_t>(nbins, n / 2 + 1));
+    // runs that fit a CTA (and single heavy bins) leave here.  Only what the
+    // launch needs is planned before it; the final buckets are listed while
+    // the pass runs.
     std::vector<SegRange> large;
     Pass Pd, Pr;
     Pd.digit = true;
@@ -1247,37 +1252,18 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     Pd.src = Pr.src = ktmp;
     Pd.dst = Pr.dst = kout;
     const uint32_t span_bins = msd || shift >= 16 ? 1u : 1u << (16 - shift);
+    // Per level-1 run: -1 if it is final, else (pass, index) of its level-2 segment.
+    std::vector<int32_t> split2(s1.size() + 1, -1);
     for (size_t g = 0; g <= s1.size(); ++g) {
         const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
         const unsigned long long sz = binpos[b1] - binpos[b0];
-        if (sz == 0) continue;
-        if (sz <= kBucketCap || b1 - b0 == 1) {
-            if (sz <= kBucketCap && sz > 1)
-                finals.push_back(final_bucket_bounded(binpos[b0], (uint32_t)sz, 0, bin_lo(b0), range_bits(b0, b1)));
-            else
-                finals.push_back(final_bucket(binpos[b0], (uint32_t)sz, 0, false));   // copy out
-            if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
-            continue;
-        }
+        if (sz <= kBucketCap || b1 - b0 == 1) continue;
         std::vector<uint32_t> st2 = group_bins(hist, b0, b1, kBucketCap / 2,
                                                std::max<uint32_t>(span_bins, (b1 - b0 + 255) / 256));
         bool single = (b1 - b0 <= 256) && st2.size() == b1 - b0 - 1;
         for (size_t j = 0; single && j < st2.size(); ++j) single = st2[j] == b0 + 1 + j;
-        // Sub-buckets of this run.
-        uint32_t lo_b = b0;
-        for (size_t j = 0; j <= st2.size(); ++j) {
-            const uint32_t hi_b = j == st2.size() ? b1 : st2[j];
-            const unsigned long long ssz = binpos[hi_b] - binpos[lo_b];
-            if (ssz >= 2) {
-                if (ssz <= kBucketCap)
-                    finals.push_back(final_bucket_bounded(binpos[lo_b], (uint32_t)ssz, 1, bin_lo(lo_b),
-                                                          range_bits(lo_b, hi_b)));
-                else
-                    large.push_back({binpos[lo_b], (uint32_t)ssz, 0ull});
-            }
-            lo_b = hi_b;
-        }
         Pass& P = single ? Pd : Pr;
+        split2[g] = (int32_t)((single ? 0u : 1u << 30) | (uint32_t)P.segs.size());
         P.segs.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
         P.starts.push_back(std::move(st2));
     }
@@ -1295,30 +1281,57 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             *levels_out = 2;
         }
     }
-    // Final buckets.
-    const FinalPlan fp = plan_finals(finals);
+    // Final buckets, into the class regions of the third window: level-1 runs
+    // that are final (from the temporary buffer) and the sub-buckets of the
+    // level-2 segments (from the output).
+    ClassLists cl;
+    cl.cap = class_cap;
+    for (int k = 0; k < kBucketClasses; ++k)
+        cl.region[k] = reinterpret_cast<FinalBucket*>(stage + capA + capB + k * class_bytes);
+    for (size_t g = 0; g <= s1.size(); ++g) {
+        const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
+        const unsigned long long sz = binpos[b1] - binpos[b0];
+        if (sz == 0) continue;
+        if (split2[g] < 0) {
+            if (sz <= kBucketCap && sz > 1)
+                cl.add(final_bucket_bounded(binpos[b0], (uint32_t)sz, 0, bin_lo(b0), range_bits(b0, b1)));
+            else
+                cl.add(final_bucket(binpos[b0], (uint32_t)sz, 0, false));   // copy out
+            if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
+            continue;
+        }
+        const Pass& P = (split2[g] >> 30) ? Pr : Pd;
+        const std::vector<uint32_t>& st2 = P.starts[split2[g] & ((1 << 30) - 1)];
+        uint32_t lo_b = b0;
+        for (size_t j = 0; j <= st2.size(); ++j) {
+            const uint32_t hi_b = j == st2.size() ? b1 : st2[j];
+            const unsigned long long ssz = binpos[hi_b] - binpos[lo_b];
+            if (ssz >= 2) {
+                if (ssz <= kBucketCap)
+                    cl.add(final_bucket_bounded(binpos[lo_b], (uint32_t)ssz, 1, bin_lo(lo_b),
+                                                range_bits(lo_b, hi_b)));
+                else
+                    large.push_back({binpos[lo_b], (uint32_t)ssz, 0ull});
+            }
+            lo_b = hi_b;
+        }
+    }
+    if (cl.overflow) return AHS_ERR_CUDA;
     {
-        Blob C{stage + capA + capB, capC};
-        size_t o_cls[kBucketClasses];
-        for (int k = 0; k < kBucketClasses; ++k)
-            o_cls[k] = C.add(fp.cls[k].data(), fp.cls[k].size() * sizeof(FinalBucket));
-        if (C.overflow()) return AHS_ERR_CUDA;
-        e = upload(C, capA + capB);
         const FinalBucket* lists[kBucketClasses];
-        uint32_t counts[kBucketClasses];
-        uint64_t keys[kBucketClasses];
-        for (int k = 0; k < kBucketClasses; ++k) {
-            lists[k] = reinterpret_cast<const FinalBucket*>(aux + capA + capB + o_cls[k]);
-            counts[k] = (uint32_t)fp.cls[k].size();
-            keys[k] = 0;
-            for (const FinalBucket& f : fp.cls[k]) keys[k] += f.size;
+        for (int k = 0; k < kBucketClasses && e == cudaSuccess; ++k) {
+            const size_t off = capA + capB + k * class_bytes;
+            lists[k] = reinterpret_cast<const FinalBucket*>(aux + off);
+            if (cl.count[k])
+                e = cudaMemcpyAsync(aux + off, stage + off, cl.count[k] * sizeof(FinalBucket),
+                                    cudaMemcpyHostToDevice, st);
         }
         if (e == cudaSuccess)
-            e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, kout, nullptr, nullptr,
+            e = launch_bucket_finish(lists, cl.count, cl.keys, ktmp, kout, kin, kout, nullptr, nullptr,
                                      nullptr, nullptr, KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st);
         if (e != cudaSuccess) return cuda_status(ctx, e);
     }
-    *buckets_out = fp.sorted;
+    *buckets_out = cl.sorted;
     if (large.empty()) return AHS_OK;
     // The pinned staging still feeds the copies above: wait before reusing it.
     e = cudaStreamSynchronize(st);
