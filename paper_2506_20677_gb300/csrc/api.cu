@@ -170,19 +170,18 @@ ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st) {
                                                                      : AHS_ERR_CUDA;
 }
 
-// The feature histogram's nbins counts, copied to the host before the
-// workspace may grow (growing it does not keep its contents).
+// The feature histogram's nbins counts, copied to the context's pinned
+// mirror before the workspace may grow (growing it does not keep its contents).
 static ahs_status host_histogram(ahs_ctx* ctx, const ahs_features_t& f, cudaStream_t st,
-                                 std::vector<unsigned long long>* out) {
+                                 HistView* out) {
+    if (f.nbins > kMaxBins) return AHS_ERR_INVALID_ARG;
     FeatureScratch fs = carve_features(ctx);
-    ahs_status rc = ensure_stage(ctx, (size_t)f.nbins * 8);
-    if (rc != AHS_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(ctx->h_stage, fs.hist, (size_t)f.nbins * 8,
+    cudaError_t e = cudaMemcpyAsync(ctx->h_hist, fs.hist, (size_t)f.nbins * 8,
                                     cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
-    out->resize(f.nbins);
-    std::memcpy(out->data(), ctx->h_stage, (size_t)f.nbins * 8);
+    out->counts = ctx->h_hist;
+    out->nbins = f.nbins;
     return AHS_OK;
 }
 
@@ -226,7 +225,7 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
     case AHS_RADIX: {
         if (s == AHS_RADIX && !vin && f.hist_shift > 0 && n >= 2 && n <= 0xffffffffull) {
             // Keys only: most significant digit first, unstable partitions.
-            std::vector<unsigned long long> hist;
+            HistView hist;
             ahs_status rc = host_histogram(ctx, f, st, &hist);
             if (rc != AHS_OK) return rc;
             const size_t need = samplesort_scratch_bytes(n, kd.bytes, false);
@@ -255,7 +254,7 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
     }
     case AHS_GENERAL: {
         if (n >= (1ull << 32)) return AHS_ERR_UNIMPLEMENTED;
-        std::vector<unsigned long long> hist;
+        HistView hist;
         const bool use_hist = !vin && f.nbins > 256;
         if (use_hist) {
             ahs_status rc = host_histogram(ctx, f, st, &hist);
@@ -341,7 +340,8 @@ ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&d, persist);
     if (e == cudaSuccess) e = cudaMemset(d, 0, persist);
     void* h = nullptr;
-    if (e == cudaSuccess) e = cudaHostAlloc(&h, persist, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&h, persist + kMaxBins * sizeof(unsigned long long),
+                                            cudaHostAllocDefault);
     for (int i = 0; e == cudaSuccess && i < 4; ++i) e = cudaEventCreate(&ctx->ev[i]);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -355,6 +355,7 @@ ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg) {
     ctx->d_err = reinterpret_cast<uint32_t*>(static_cast<char*>(d) + 256);
     ctx->h_rec = static_cast<DevFeatures*>(h);
     ctx->h_err = reinterpret_cast<uint32_t*>(static_cast<char*>(h) + 256);
+    ctx->h_hist = reinterpret_cast<unsigned long long*>(static_cast<char*>(h) + persist);
     if (ctx->cfg.model_path) {
         std::string why;
         if (!ctx->model.load(ctx->cfg.model_path, &why)) {

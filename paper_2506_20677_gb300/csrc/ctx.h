@@ -26,9 +26,10 @@ struct ahs_ctx {
     // Persistent device block: feature record + error word (zeroed at create).
     ahs::DevFeatures* d_rec = nullptr;
     uint32_t* d_err = nullptr;
-    // Pinned host mirror of the persistent block.
+    // Pinned host mirror of the persistent block, and of the feature histogram.
     ahs::DevFeatures* h_rec = nullptr;
     uint32_t* h_err = nullptr;
+    unsigned long long* h_hist = nullptr;   // kMaxBins counts
 
     // Growable device workspace.
     void* ws = nullptr;
@@ -69,6 +70,15 @@ ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st);
 // Grow the auxiliary device buffer / pinned host staging (may synchronise).
 ahs_status ensure_aux(ahs_ctx* ctx, size_t bytes);
 ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes);
+// The host copy of the feature histogram (pinned, owned by the context).
+struct HistView {
+    const unsigned long long* counts = nullptr;
+    uint32_t nbins = 0;
+    size_t size() const { return nbins; }
+    bool empty() const { return nbins == 0; }
+    unsigned long long operator[](size_t i) const { return counts[i]; }
+};
+
 // General path: stable sample sort with shared-memory bucket sorts.  scratch is
 // samplesort_scratch_bytes() of workspace.  Synchronises `st` once per level.
 // Keys only, with `hist` (the host copy of the feature histogram, bins of
@@ -79,7 +89,7 @@ ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes);
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
                           uint32_t* levels_out, uint32_t* buckets_out,
-                          const std::vector<unsigned long long>* hist = nullptr,
+                          const HistView* hist = nullptr,
                           uint64_t min_ord = 0, uint32_t shift = 0, uint32_t group = 0);
 
 // Keys-only radix sort, most significant digit first: two partition passes by
@@ -87,7 +97,7 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
 // from `hist`, the host copy of the histogram, bin = (ord(x) - min_ord) >> shift),
 // then per-bin shared-memory sorts.  scratch: samplesort_scratch_bytes().
 ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
-                         uint64_t min_ord, const std::vector<unsigned long long>& hist,
+                         uint64_t min_ord, const HistView& hist,
                          uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
                          uint32_t* levels_out, uint32_t* buckets_out);
 

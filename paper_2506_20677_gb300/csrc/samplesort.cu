@@ -985,7 +985,7 @@ void range_splitters(const std::vector<K>& thr, K* out) {
 // Host: greedy grouping of bins [b0, b1) into at most 256 runs of about
 // `target` keys and at most `max_bins` bins (a bin heavier than the target
 // is a run of its own).  Returns the first bin of every run after the first.
-std::vector<uint32_t> group_bins(const std::vector<unsigned long long>& hist, uint32_t b0,
+std::vector<uint32_t> group_bins(const HistView& hist, uint32_t b0,
                                  uint32_t b1, unsigned long long target,
                                  uint32_t max_bins = 0xffffffffu) {
     std::vector<uint32_t> starts;
@@ -1092,7 +1092,7 @@ struct ClassLists {
 
 template <typename K>
 ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,
-                       const std::vector<unsigned long long>& hist, uint32_t shift, bool msd,
+                       const HistView& hist, uint32_t shift, bool msd,
                        uint32_t group, void* scratch, cudaStream_t st, uint32_t* levels_out,
                        uint32_t* buckets_out) {
     K* ktmp = static_cast<K*>(scratch);
@@ -1390,7 +1390,7 @@ ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const u
 }
 
 ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
-                         uint64_t min_ord, const std::vector<unsigned long long>& hist,
+                         uint64_t min_ord, const HistView& hist,
                          uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
                          uint32_t* levels_out, uint32_t* buckets_out) {
     *levels_out = 0;
@@ -1407,7 +1407,7 @@ ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, 
 ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                           uint32_t* vout, uint64_t n, KeyDesc kd, void* scratch, cudaStream_t st,
                           uint32_t* levels_out, uint32_t* buckets_out,
-                          const std::vector<unsigned long long>* hist, uint64_t min_ord,
+                          const HistView* hist, uint64_t min_ord,
                           uint32_t shift, uint32_t group) {
     *levels_out = 0;
     *buckets_out = 0;
