@@ -87,9 +87,10 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
     ahs_status rc = ensure_workspace(ctx, features_region(ctx->sms) + align256((kMaxBins + 1) * 8));
     if (rc != AHS_OK) return rc;
     FeatureScratch s = carve_features(ctx);
+    // K3 writes the record and the histogram into the pinned mirrors.
+    s.host_rec = ctx->h_rec;
+    s.host_hist = ctx->h_hist;
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->h_rec, ctx->d_rec, sizeof(DevFeatures), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     to_public(*ctx->h_rec, kd, out);
@@ -158,7 +159,7 @@ ahs_status ensure_stage(ahs_ctx* ctx, size_t bytes) {
 }
 
 ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = launch_transfer(ctx->h_err, ctx->d_err, sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     const uint32_t code = *ctx->h_err;
@@ -170,16 +171,11 @@ ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st) {
                                                                      : AHS_ERR_CUDA;
 }
 
-// The feature histogram's nbins counts, copied to the context's pinned
-// mirror before the workspace may grow (growing it does not keep its contents).
-static ahs_status host_histogram(ahs_ctx* ctx, const ahs_features_t& f, cudaStream_t st,
+// The feature histogram's nbins counts: the pinned mirror that the feature
+// pass filled (it stays valid when the workspace grows).
+static ahs_status host_histogram(ahs_ctx* ctx, const ahs_features_t& f, cudaStream_t,
                                  HistView* out) {
     if (f.nbins > kMaxBins) return AHS_ERR_INVALID_ARG;
-    FeatureScratch fs = carve_features(ctx);
-    cudaError_t e = cudaMemcpyAsync(ctx->h_hist, fs.hist, (size_t)f.nbins * 8,
-                                    cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_status(ctx, e);
     out->counts = ctx->h_hist;
     out->nbins = f.nbins;
     return AHS_OK;

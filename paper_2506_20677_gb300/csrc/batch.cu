@@ -360,7 +360,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
     std::memcpy(hsb, chunks.data(), chunks.size() * sizeof(SegChunk));
     std::memcpy(hsb + b_chunks, hsmall.data(), hsmall.size() * sizeof(HistSeg));
     std::memcpy(hsb + b_chunks + b_hs, hlarge.data(), hlarge.size() * sizeof(HistSeg));
-    cudaError_t e = cudaMemcpyAsync(d_chunks, hsb, b_chunks + b_hs + b_hl, cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_transfer(d_chunks, hsb, b_chunks + b_hs + b_hl, st);
     const auto t0 = clock::now();
     uint64_t keys_small = 0, keys_large = 0;
     for (const HistSeg& h : hsmall) keys_small += h.size;
@@ -396,7 +396,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
             e = cudaLaunchKernelEx(&cfg, seg_hist_large<K>, kin, (const HistSeg*)d_hl, flip, d_feat);
         }
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hsb, d_feat, (size_t)n_seg * sizeof(SegFeat), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = launch_transfer(hsb, d_feat, (size_t)n_seg * sizeof(SegFeat), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     const auto t1 = clock::now();
@@ -468,8 +468,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
         if (rc == AHS_OK) rc = ensure_stage(ctx, counting.size() * sizeof(CountSeg));
         if (rc != AHS_OK) return rc;
         std::memcpy(ctx->h_stage, counting.data(), counting.size() * sizeof(CountSeg));
-        e = cudaMemcpyAsync(ctx->aux, ctx->h_stage, counting.size() * sizeof(CountSeg),
-                            cudaMemcpyHostToDevice, st);
+        e = launch_transfer(ctx->aux, ctx->h_stage, counting.size() * sizeof(CountSeg), st);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(seg_counting<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (kCountMaxBins + 1) * 4);

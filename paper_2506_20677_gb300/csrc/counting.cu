@@ -4,6 +4,8 @@
 // written run by run.  The keys are not read again: value min + j fills
 // positions [prefix[j], prefix[j+1]).  Output order for keys only is unique,
 // so the stable reverse scan of Listing 2 and this fill give the same array.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "trace.h"
@@ -174,6 +176,41 @@ cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, c
     } else {
         copy32_scalar<<<grid_for(words, 1024, sms, 8), 256, 0, st>>>((uint32_t*)dst,
                                                                     (const uint32_t*)src, words);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256)
+transfer_words(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src,
+               uint64_t words) {
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < words; i += stride)
+        dst[i] = src[i];
+}
+
+__global__ void __launch_bounds__(256)
+transfer_bytes(unsigned char* __restrict__ dst, const unsigned char* __restrict__ src,
+               uint64_t bytes) {
+    for (uint64_t i = threadIdx.x; i < bytes; i += 256) dst[i] = src[i];
+}
+
+cudaError_t launch_transfer(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0 || dst == src) return cudaSuccess;
+    TraceScope ts("transfer", 0, st);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst), b = reinterpret_cast<uintptr_t>(src);
+    const size_t words = bytes / 8;
+    if (((a | b) & 7u) == 0 && words) {
+        // Work lists are kilobytes to a few megabytes: up to 64 CTAs keep
+        // enough host reads in flight.
+        transfer_words<<<(uint32_t)std::min<uint64_t>(ceil_div(words, 256), 64), 256, 0, st>>>(
+            static_cast<unsigned long long*>(dst), static_cast<const unsigned long long*>(src), words);
+        if (bytes % 8)
+            transfer_bytes<<<1, 256, 0, st>>>(static_cast<unsigned char*>(dst) + words * 8,
+                                             static_cast<const unsigned char*>(src) + words * 8,
+                                             bytes % 8);
+    } else {
+        transfer_bytes<<<1, 256, 0, st>>>(static_cast<unsigned char*>(dst),
+                                         static_cast<const unsigned char*>(src), bytes);
     }
     return cudaGetLastError();
 }

@@ -267,10 +267,13 @@ k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint
     else k2_replicated<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
 }
 
+// host_rec / host_hist (optional): pinned host mirrors of the record and of
+// the histogram, written here so that the host reads them without a copy.
 __global__ void __launch_bounds__(256)
 k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
            DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
-           double* __restrict__ partials) {
+           double* __restrict__ partials, DevFeatures* host_rec,
+           unsigned long long* host_hist) {
     const uint32_t nb = rec->nbins;
     const uint32_t nslabs = nb > kU32Bins ? k2_grid / 2 : k2_grid;   // see K2's two layouts
     const uint32_t j = blockIdx.x * 256 + threadIdx.x;
@@ -287,6 +290,7 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
         }
         for (; c < nslabs; ++c) tot += slabs[(size_t)c * kMaxBins + j];
         hist[j] = tot;
+        if (host_hist) host_hist[j] = tot;
         if (tot) {
             const double p = (double)tot / (double)n;
             term = -p * log2(p);
@@ -311,6 +315,7 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
     rec->entropy = H;
     rec->entropy_norm = nb > 1 ? H / log2((double)nb) : 0.0;
     rec->k3_done = 0;
+    if (host_rec) *host_rec = *rec;
 }
 
 template <typename K>
@@ -349,7 +354,8 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
     }
     {
         TraceScope ts("features_entropy", 0, st);
-        k3_entropy<<<kEntropyBlocks, 256, 0, st>>>(s.slabs, g2, n, s.rec, s.hist, s.ent_partials);
+        k3_entropy<<<kEntropyBlocks, 256, 0, st>>>(s.slabs, g2, n, s.rec, s.hist, s.ent_partials,
+                                                   s.host_rec, s.host_hist);
     }
     return cudaGetLastError();
 }

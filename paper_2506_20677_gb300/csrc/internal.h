@@ -54,6 +54,9 @@ struct FeatureScratch {
     uint32_t* slabs;                  // hist_blocks x kMaxBins
     unsigned long long* hist;         // kMaxBins exact counts (u64)
     double* ent_partials;             // kEntropyBlocks
+    // Optional pinned host mirrors that K3 fills (null: device copies only).
+    DevFeatures* host_rec = nullptr;
+    unsigned long long* host_hist = nullptr;   // nbins counts
 };
 uint32_t k1_blocks(uint64_t n, int sms);
 size_t features_scratch_bytes(int sms);
@@ -71,6 +74,11 @@ cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFea
 cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st);
 // Zero `words` 32-bit words.
 cudaError_t launch_zero32(void* dst, uint64_t words, int sms, cudaStream_t st);
+// Move `bytes` between pinned host memory (mapped into the device's address
+// space) and device memory with a kernel, not a copy engine: a sort's small
+// uploads and read-backs then never queue behind bulk copies the caller runs
+// on the copy engines at the same time.
+cudaError_t launch_transfer(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 // --------------------------------------------------------------------- radix
 struct RadixPlan {

@@ -696,7 +696,7 @@ ahs_status upload_level(ahs_ctx* ctx, Level& L, uint32_t key_bytes, bool split, 
     std::memcpy(hs, L.segs.data(), ns * sizeof(SegDesc));
     std::memcpy(hs + b_segs, L.tiles.data(), nt * sizeof(TileDesc));
     std::memcpy(hs + b_segs + b_tiles, L.chunks.data(), nc * sizeof(ChunkDesc));
-    cudaError_t e = cudaMemcpyAsync(L.d_segs, hs, b_segs + b_tiles + b_chunks, cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_transfer(L.d_segs, hs, b_segs + b_tiles + b_chunks, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
 }
@@ -719,7 +719,7 @@ cudaError_t partition(const Level& L, const K* src, K* dst, const uint32_t* vsrc
             src, L.d_segs, level, flip, spl, L.nsplit);
     }
     if (!VALS && fast) {
-        cudaError_t e = cudaMemsetAsync(L.seg_tot, 0, (size_t)ns * kCols * 4, st);
+        cudaError_t e = launch_zero32(L.seg_tot, (uint64_t)ns * kCols, sms, st);
         if (e != cudaSuccess) return e;
         {
             TraceScope ts(MODE == kSplit ? "sample_count" : "segradix_count", keys, st);
@@ -811,7 +811,7 @@ ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, 
         for (const FinalBucket& f : cls[k]) keys[k] += f.size;
         at += cls[k].size();
     }
-    cudaError_t e = cudaMemcpyAsync(df, hf, nf * sizeof(FinalBucket), cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_transfer(df, hf, nf * sizeof(FinalBucket), st);
     if (e == cudaSuccess)
         e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
                                  vtmp, vout, vin, vout, kd, st);
@@ -861,8 +861,8 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
         if (e == cudaSuccess) rc = ensure_stage(ctx, 2 * bread);
         if (rc != AHS_OK) return rc;
         char* hs = static_cast<char*>(ctx->h_stage);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hs, L.seg_tot, bread, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hs + bread, L.seg_base, bread, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = launch_transfer(hs, L.seg_tot, bread, st);
+        if (e == cudaSuccess) e = launch_transfer(hs + bread, L.seg_base, bread, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(ctx, e);
         const uint32_t* tot = reinterpret_cast<const uint32_t*>(hs);
@@ -960,7 +960,7 @@ ahs_status upload_msd(ahs_ctx* ctx, Level& L, const std::vector<uint32_t>& curso
     std::memcpy(hs + b_segs, L.tiles.data(), nt * sizeof(TileDesc));
     if (!cursor.empty()) std::memcpy(hs + b_segs + b_tiles, cursor.data(), cursor.size() * 4);
     if (splitter_bytes) std::memcpy(hs + b_segs + b_tiles + b_cur, splitters, splitter_bytes);
-    cudaError_t e = cudaMemcpyAsync(p, hs, total, cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_transfer(p, hs, total, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
 }
@@ -1025,7 +1025,7 @@ ahs_status finish_large(ahs_ctx* ctx, const std::vector<SegRange>& large, K* kou
     rc = ensure_stage(ctx, 2 * ns * 8);
     if (rc != AHS_OK) return rc;
     std::memcpy(ctx->h_stage, seed.data(), 2 * ns * 8);
-    cudaError_t e = cudaMemcpyAsync(d_mm, ctx->h_stage, 2 * ns * 8, cudaMemcpyHostToDevice, st);
+    cudaError_t e = launch_transfer(d_mm, ctx->h_stage, 2 * ns * 8, st);
     if (e == cudaSuccess) {
         uint64_t lk = 0;
         for (const SegRange& x : large) lk += x.size;
@@ -1033,7 +1033,7 @@ ahs_status finish_large(ahs_ctx* ctx, const std::vector<SegRange>& large, K* kou
         seg_tile_minmax<K><<<(uint32_t)L.tiles.size(), kThreads, 0, st>>>(kout, L.d_tiles, flip, d_mm);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_stage, d_mm, 2 * ns * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = launch_transfer(ctx->h_stage, d_mm, 2 * ns * 8, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     const unsigned long long* mm = static_cast<const unsigned long long*>(ctx->h_stage);
@@ -1184,7 +1184,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         return pl;
     };
     auto upload = [&](const Blob& blob, size_t window) -> cudaError_t {
-        return cudaMemcpyAsync(aux + window, stage + window, blob.used, cudaMemcpyHostToDevice, st);
+        return launch_transfer(aux + window, stage + window, blob.used, st);
     };
     auto launch = [&](const Pass& P, const Placed& pl, size_t window) -> cudaError_t {
         if (pl.ns > kSegCache) return cudaErrorInvalidValue;   // level-1 runs are at most 256
@@ -1323,8 +1323,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             const size_t off = capA + capB + k * class_bytes;
             lists[k] = reinterpret_cast<const FinalBucket*>(aux + off);
             if (cl.count[k])
-                e = cudaMemcpyAsync(aux + off, stage + off, cl.count[k] * sizeof(FinalBucket),
-                                    cudaMemcpyHostToDevice, st);
+                e = launch_transfer(aux + off, stage + off, cl.count[k] * sizeof(FinalBucket), st);
         }
         if (e == cudaSuccess)
             e = launch_bucket_finish(lists, cl.count, cl.keys, ktmp, kout, kin, kout, nullptr, nullptr,
