@@ -771,49 +771,67 @@ cudaError_t set_attrs() {
     return e;
 }
 
+// Final buckets written straight into the pinned staging, one region of
+// `cap` entries per size class of the bucket kernels; unsorted (copy) buckets
+// larger than kCopyChunk are split so that many CTAs share them.
+struct ClassLists {
+    FinalBucket* region[kBucketClasses];
+    size_t cap = 0;
+    uint32_t count[kBucketClasses] = {};
+    uint64_t keys[kBucketClasses] = {};
+    uint32_t sorted = 0;
+    bool overflow = false;
+    void put(int k, const FinalBucket& f) {
+        if (count[k] >= cap) { overflow = true; return; }
+        region[k][count[k]++] = f;
+        keys[k] += f.size;
+    }
+    void add(const FinalBucket& f) {
+        if (!f.sort && f.size > kCopyChunk) {
+            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
+                put(0, final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
+            return;
+        }
+        put(f.sort ? (int)bucket_class(f.size) : 0, f);
+        sorted += f.sort;
+    }
+};
+
+
 // Upload a final-bucket list to the auxiliary buffer and run the bucket
 // sorts (one launch per size class); synchronises before returning so the
 // pinned staging can be reused.
 ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, const void* ktmp,
                           const void* kout, const void* kin, const uint32_t* vtmp, uint32_t* vout,
                           const uint32_t* vin, KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
-    std::vector<FinalBucket> cls[kBucketClasses];
-    uint32_t nsorted = 0;
-    for (const FinalBucket& f : finals) {
-        if (!f.sort && f.size > kCopyChunk) {
-            // A large copy (an equality bucket of a heavy key) is split so
-            // that many CTAs share it.
-            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
-                cls[0].push_back(final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
-            continue;
-        }
-        cls[f.sort ? bucket_class(f.size) : 0].push_back(f);
-        nsorted += f.sort;
+    // Entries per class (a large copy, the equality bucket of a heavy key, is
+    // split so that many CTAs share it), then the lists written in place.
+    size_t per[kBucketClasses] = {};
+    for (const FinalBucket& f : finals)
+        per[f.sort ? bucket_class(f.size) : 0] += (!f.sort && f.size > kCopyChunk) ? ceil_div(f.size, kCopyChunk) : 1;
+    size_t nf = 0, at[kBucketClasses];
+    for (int k = 0; k < kBucketClasses; ++k) {
+        at[k] = nf;
+        nf += per[k];
     }
-    size_t nf = 0;
-    for (int k = 0; k < kBucketClasses; ++k) nf += cls[k].size();
-    if (sorted) *sorted = nsorted;
+    if (sorted) *sorted = 0;
     if (nf == 0) return AHS_OK;
     ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
     if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
     if (rc != AHS_OK) return rc;
     FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
     FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
+    ClassLists cl;
+    cl.cap = nf;
+    for (int k = 0; k < kBucketClasses; ++k) cl.region[k] = hf + at[k];
+    for (const FinalBucket& f : finals) cl.add(f);
+    if (cl.overflow) return AHS_ERR_CUDA;
+    if (sorted) *sorted = cl.sorted;
     const FinalBucket* lists[kBucketClasses];
-    uint32_t counts[kBucketClasses];
-    uint64_t keys[kBucketClasses];
-    size_t at = 0;
-    for (int k = 0; k < kBucketClasses; ++k) {
-        std::memcpy(hf + at, cls[k].data(), cls[k].size() * sizeof(FinalBucket));
-        lists[k] = df + at;
-        counts[k] = (uint32_t)cls[k].size();
-        keys[k] = 0;
-        for (const FinalBucket& f : cls[k]) keys[k] += f.size;
-        at += cls[k].size();
-    }
+    for (int k = 0; k < kBucketClasses; ++k) lists[k] = df + at[k];
     cudaError_t e = launch_transfer(df, hf, nf * sizeof(FinalBucket), st);
     if (e == cudaSuccess)
-        e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
+        e = launch_bucket_finish(lists, cl.count, cl.keys, ktmp, kout, kin, const_cast<void*>(kout),
                                  vtmp, vout, vin, vout, kd, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
@@ -833,6 +851,8 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
     if (e != cudaSuccess) return cuda_status(ctx, e);
 
     std::vector<FinalBucket> finals;
+    // Buckets hold a CTA's capacity / 2 keys on average: reserve for that.
+    finals.reserve(extra.size() + segs.size() + 2 * (n_total / (kBucketCap / 2)) + 64);
     for (const SegRange& x : extra)
         finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
     std::vector<SegRange> open;
@@ -1064,31 +1084,6 @@ struct Blob {
     bool overflow() const { return used > cap; }
 };
 
-// Final buckets written straight into the pinned staging, one region of
-// `cap` entries per size class of the bucket kernels; unsorted (copy) buckets
-// larger than kCopyChunk are split so that many CTAs share them.
-struct ClassLists {
-    FinalBucket* region[kBucketClasses];
-    size_t cap = 0;
-    uint32_t count[kBucketClasses] = {};
-    uint64_t keys[kBucketClasses] = {};
-    uint32_t sorted = 0;
-    bool overflow = false;
-    void put(int k, const FinalBucket& f) {
-        if (count[k] >= cap) { overflow = true; return; }
-        region[k][count[k]++] = f;
-        keys[k] += f.size;
-    }
-    void add(const FinalBucket& f) {
-        if (!f.sort && f.size > kCopyChunk) {
-            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
-                put(0, final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
-            return;
-        }
-        put(f.sort ? (int)bucket_class(f.size) : 0, f);
-        sorted += f.sort;
-    }
-};
 
 template <typename K>
 ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, K mn,

@@ -41,10 +41,28 @@ inline FinalBucket final_bucket_bounded(unsigned long long begin, uint32_t size,
     return FinalBucket{begin, lo, size, where, 1, (uint8_t)bits, 0};
 }
 
+// Class caps are multiples of 512 keys: the class of a size is a lookup on
+// (size - 1) / 512 (sizes past the last cap take the last class).
+struct BucketClassTable {
+    uint8_t c[kBucketCap / 512];
+    constexpr BucketClassTable() : c{} {
+        for (uint32_t i = 0; i < kBucketCap / 512; ++i) {
+            uint8_t k = kBucketClasses - 1;
+            for (int j = kBucketClasses - 1; j >= 0; --j)
+                if ((i + 1) * 512 <= kBucketClassCap[j]) k = (uint8_t)j;
+            c[i] = k;
+        }
+    }
+};
+static_assert([] {
+    for (uint32_t cap : kBucketClassCap)
+        if (cap % 512) return false;
+    return true;
+}(), "bucket class caps are multiples of 512");
 inline uint32_t bucket_class(uint32_t size) {
-    for (int c = 0; c < kBucketClasses - 1; ++c)
-        if (size <= kBucketClassCap[c]) return c;
-    return kBucketClasses - 1;
+    static constexpr BucketClassTable t{};
+    const uint32_t i = size ? (size - 1) / 512 : 0;
+    return i < kBucketCap / 512 ? t.c[i] : kBucketClasses - 1;
 }
 cudaError_t launch_bucket_finish(const FinalBucket* d_lists[kBucketClasses],
                                  const uint32_t counts[kBucketClasses],
