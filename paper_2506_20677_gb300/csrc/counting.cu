@@ -46,6 +46,20 @@ __device__ __forceinline__ uint32_t bin_of(const unsigned long long* __restrict_
     return lo;
 }
 
+// The same, for a position known to lie in bin lo or later: steps of 1, 2,
+// 4, ... from lo, then a binary search in the last step (a few dependent
+// loads when bins hold many keys).
+__device__ __forceinline__ uint32_t bin_from(const unsigned long long* __restrict__ prefix,
+                                             uint64_t p, uint32_t lo, uint32_t nb) {
+    uint32_t step = 1;
+    while (lo + step < nb && prefix[lo + step] <= p) {
+        lo += step;
+        step <<= 1;
+    }
+    const uint32_t hi = lo + step - 1 < nb - 1 ? lo + step - 1 : nb - 1;
+    return bin_of(prefix, p, lo, hi);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kFillThreads)
 counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
@@ -61,21 +75,29 @@ counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
             out[p] = (K)(mn + bin_of(prefix, p, 0, nb - 1)) ^ flip;
         }
     }
-    __shared__ uint32_t s_lo, s_hi;
+    // Each block fills a contiguous run of chunks.  Thread 0 finds the bins of
+    // chunk c + 1 (from where chunk c ends) while the block writes chunk c.
+    __shared__ uint32_t s_lo[2], s_hi[2];
     K* body = out + head;
     const uint64_t nchunks = ceil_div(nvec, kChunk);
-    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const uint64_t p0 = head + c * kChunk * V;
-            uint64_t vend = (c + 1) * kChunk;
-            vend = vend < nvec ? vend : nvec;
-            const uint64_t p1 = head + vend * V - 1;
-            s_lo = bin_of(prefix, p0, 0, nb - 1);
-            s_hi = bin_of(prefix, p1, s_lo, nb - 1);
-        }
-        __syncthreads();
-        const uint32_t lo = s_lo, hi = s_hi;
-        __syncthreads();
+    const uint64_t per = ceil_div(nchunks, (uint64_t)gridDim.x);
+    const uint64_t c0 = (uint64_t)blockIdx.x * per;
+    const uint64_t c1 = c0 + per < nchunks ? c0 + per : nchunks;
+    auto bins = [&](uint64_t c, uint32_t from, int slot) {   // thread 0
+        const uint64_t p0 = head + c * kChunk * V;
+        uint64_t vend = (c + 1) * kChunk;
+        vend = vend < nvec ? vend : nvec;
+        const uint64_t p1 = head + vend * V - 1;
+        const uint32_t lo = bin_from(prefix, p0, from, nb);
+        s_lo[slot] = lo;
+        s_hi[slot] = bin_from(prefix, p1, lo, nb);
+    };
+    if (threadIdx.x == 0 && c0 < c1) bins(c0, bin_of(prefix, head + c0 * kChunk * V, 0, nb - 1), 0);
+    __syncthreads();
+    for (uint64_t c = c0; c < c1; ++c) {
+        const int slot = (int)((c - c0) & 1);
+        const uint32_t lo = s_lo[slot], hi = s_hi[slot];
+        if (threadIdx.x == 0 && c + 1 < c1) bins(c + 1, hi, slot ^ 1);
 #pragma unroll
         for (int u = 0; u < kFillUnroll; ++u) {
             const uint64_t v = c * kChunk + (uint64_t)u * kFillThreads + threadIdx.x;
@@ -91,6 +113,7 @@ counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
             if constexpr (sizeof(K) == 4) __stcs(reinterpret_cast<uint4*>(body + v * V), r.v);
             else __stcs(reinterpret_cast<ulonglong2*>(body + v * V), r.v);
         }
+        __syncthreads();   // publishes chunk c + 1's bins; slot `slot` is free again
     }
 }
 
