@@ -101,16 +101,18 @@ ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, 
                          uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
                          uint32_t* levels_out, uint32_t* buckets_out);
 
-// Levels of the histogram-guided partitions whose scatter aggregates the slot
-// atomics of lanes sharing lane 0's bucket (measured on GB300: it pays where
-// a warp often holds a large group on one bucket counter but not the whole
-// warp, and costs elsewhere).  Level 1: runs broken by displaced keys (few
-// descents); wholly ordered warps take the plain path's one-atomic case.
-// Level 2: a skewed histogram (normalised entropy below 0.9), whose heavy
-// keys crowd the buckets of a level-1 run.
-constexpr uint32_t kGroupLevel1 = 1, kGroupLevel2 = 2;
+// Which partition levels aggregate the slot atomics of lanes that share a
+// bucket (measured on GB300: it pays where the lanes of a warp row often
+// share buckets without the whole row doing so, and costs up to 2.5x where
+// they rarely do).  The feature record gives level 1 for inputs of runs
+// broken by displaced keys (few descents; wholly ordered rows take the plain
+// path's one-atomic case).  The histogram adds a level when two random keys
+// of one bucket of the level before fall in the same bucket with probability
+// kGroupCollide or more (frequent keys).
+constexpr uint32_t kGroupLevel1 = 1;
+constexpr double kGroupCollide = 0.25;
 inline uint32_t group_slots(const ahs_features_t& f) {
-    return (f.descents < f.n / 4 ? kGroupLevel1 : 0u) | (f.entropy_norm < 0.9 ? kGroupLevel2 : 0u);
+    return f.descents < f.n / 4 ? kGroupLevel1 : 0u;
 }
 
 }  // namespace ahs

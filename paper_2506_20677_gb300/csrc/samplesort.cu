@@ -503,10 +503,10 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
         // A warp whose 32 keys share a bucket (runs of presorted input) takes
         // its 32 slots with one atomic instead of 32 on the same counter.
-        // GROUP (inputs with runs or frequent keys): likewise the lanes that
-        // share lane 0's bucket, when they are a quarter of the warp or more.
-        // Lane 0 holds the warp's first key, so a lane past the tile never
-        // leads a group of valid lanes.
+        // GROUP (rows whose lanes often share buckets): every set of lanes
+        // with one bucket takes its slots by one atomic of its lowest lane.
+        // The match costs more the more distinct buckets a row holds, so the
+        // host takes this variant only where lanes collide often.
         const uint32_t lane = lane_id();
         K key[IPT];
         uint32_t br[IPT];
@@ -518,18 +518,12 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
             uint32_t r = 0;
             if constexpr (GROUP) {
-                const uint32_t m0 = __ballot_sync(AHS_FULL_MASK, b == b0);
-                if (b0 < kCols && __popc(m0) >= 8) {
-                    if (b == b0) {
-                        uint32_t base = 0;
-                        if (lane == 0) base = atomicAdd(&S.hist[b0], (uint32_t)__popc(m0));
-                        r = __shfl_sync(m0, base, 0) + __popc(m0 & lanemask_lt());
-                    } else if (b < kCols) {
-                        r = atomicAdd(&S.hist[b], 1u);
-                    }
-                } else if (b < kCols) {
-                    r = atomicAdd(&S.hist[b], 1u);
-                }
+                (void)b0;
+                const uint32_t m = __match_any_sync(AHS_FULL_MASK, b);
+                const uint32_t leader = __ffs(m) - 1;
+                uint32_t base = 0;
+                if (lane == leader && b < kCols) base = atomicAdd(&S.hist[b], (uint32_t)__popc(m));
+                r = __shfl_sync(AHS_FULL_MASK, base, leader) + __popc(m & lanemask_lt());
             } else {
                 if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
                     uint32_t base = 0;
@@ -1223,7 +1217,14 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         P1.starts.push_back(s1);
         P1.digit = blocks;
         P1.dshift = shift + 8;
-        P1.group = (group & kGroupLevel1) != 0;
+        // Probability that two random keys share a level-1 bucket.
+        double d1 = 0.0;
+        for (size_t g = 0; g <= s1.size(); ++g) {
+            const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
+            const double share = (double)(binpos[b1] - binpos[b0]) / (double)n;
+            d1 += share * share;
+        }
+        P1.group = (group & kGroupLevel1) != 0 || d1 >= kGroupCollide;
         P1.src = kin;
         P1.dst = ktmp;
         Blob A{stage, capA};
@@ -1242,7 +1243,20 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     std::vector<SegRange> large;
     Pass Pd, Pr;
     Pd.digit = true;
-    Pd.group = Pr.group = (group & kGroupLevel2) != 0;
+    {
+        // Probability that two random keys of one level-1 bucket share a bin.
+        double d2 = 0.0;
+        for (size_t g = 0; g <= s1.size(); ++g) {
+            const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
+            const unsigned long long cg = binpos[b1] - binpos[b0];
+            if (cg == 0) continue;
+            double sq = 0.0;
+            for (uint32_t b = b0; b < b1; ++b) sq += (double)hist[b] * (double)hist[b];
+            d2 += sq / (double)cg;
+        }
+        d2 /= (double)n;
+        Pd.group = Pr.group = d2 >= kGroupCollide;
+    }
     Pd.dshift = shift;
     Pd.src = Pr.src = ktmp;
     Pd.dst = Pr.dst = kout;
