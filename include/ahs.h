@@ -126,6 +126,10 @@ typedef struct {
 typedef struct {
     ahs_strategy strategy;       /* the strategy that ran */
     int32_t features_valid;      /* 1 if features below were computed */
+    /* With AHS_AUTO under a profile that returns ordered inputs as they are
+     * (sorted_identity: GB300, MODEL, or CUSTOM thresholds that set it), an
+     * input found in order (descents == 0) gets no histogram pass: its
+     * entropy_bits and entropy_norm are NaN. */
     ahs_features_t features;
     uint32_t passes;             /* radix digit passes run / sample-sort partition levels */
     uint32_t buckets;            /* final buckets sorted in shared memory (general path) */

@@ -81,7 +81,7 @@ void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out) {
 }
 
 ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
-                        cudaStream_t st, ahs_features_t* out) {
+                        cudaStream_t st, ahs_features_t* out, bool skip_sorted) {
     // Room for the counting sort's prefix too: that strategy reads the
     // histogram in place, and growing the workspace would not keep it.
     ahs_status rc = ensure_workspace(ctx, features_region(ctx->sms) + align256((kMaxBins + 1) * 8));
@@ -90,11 +90,27 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
     // K3 writes the record and the histogram into the pinned mirrors.
     s.host_rec = ctx->h_rec;
     s.host_hist = ctx->h_hist;
+    s.skip_sorted = skip_sorted;
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     to_public(*ctx->h_rec, kd, out);
     return AHS_OK;
+}
+
+// Whether AUTO selection under the context's profile returns an input already
+// in order as it is (IDENTITY) whatever its entropy.
+bool sorted_identity(const ahs_ctx* ctx) {
+    switch (ctx->cfg.select_mode) {
+    case AHS_SEL_CUSTOM:
+        return ctx->custom.sorted_identity != 0;
+    case AHS_SEL_MODEL:   // ordered inputs take the rules (GB300 profile) before the trees
+        return true;
+    default: {
+        ahs_thresholds_t t;
+        return profile_thresholds(ctx->cfg.select_mode, &t) == AHS_OK && t.sorted_identity != 0;
+    }
+    }
 }
 
 ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload) {
@@ -498,7 +514,10 @@ ahs_status ahs_sort(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
 
     if (timing) cudaEventRecord(ctx->ev[0], st);
     ahs_features_t f;
-    ahs_status rc = run_features(ctx, d_keys_in, n, kd, st, &f);
+    // A profile that returns ordered inputs as they are needs no histogram
+    // for one: the feature pass skips it when K1 finds no descent.
+    ahs_status rc = run_features(ctx, d_keys_in, n, kd, st, &f,
+                                 force == AHS_AUTO && sorted_identity(ctx));
     if (rc != AHS_OK) return rc;
     if (timing) cudaEventRecord(ctx->ev[1], st);
 

@@ -55,8 +55,10 @@ namespace ahs {
 ahs_status ensure_workspace(ahs_ctx* ctx, size_t bytes);
 ahs_status cuda_status(ahs_ctx* ctx, cudaError_t e);
 // Features into ctx->h_rec (synchronises the stream); scratch at ctx->ws.
+// skip_sorted: an input found in order gets no histogram (entropy NaN); for
+// callers that then return it as it is.
 ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
-                        cudaStream_t st, ahs_features_t* out);
+                        cudaStream_t st, ahs_features_t* out, bool skip_sorted = false);
 void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out);
 ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload);
 // Run one strategy on device-resident inputs whose features are in ctx->d_rec

@@ -258,8 +258,9 @@ __device__ __forceinline__ void k2_split(const K* __restrict__ keys, uint64_t n,
 template <typename K>
 __global__ void __launch_bounds__(kHistThreads, 1)
 k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
-             const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs) {
+             const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs, int skip_sorted) {
     extern __shared__ __align__(16) uint32_t sm32[];
+    if (skip_sorted && rec->descents == 0) return;   // block-uniform
     const K mn = (K)rec->min_ord;
     const uint32_t s = rec->shift;
     const uint32_t nb = rec->nbins;
@@ -273,7 +274,16 @@ __global__ void __launch_bounds__(256)
 k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
            DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
            double* __restrict__ partials, DevFeatures* host_rec,
-           unsigned long long* host_hist) {
+           unsigned long long* host_hist, int skip_sorted) {
+    if (skip_sorted && rec->descents == 0) {
+        // K2 counted nothing: no histogram, and the entropy is marked missing.
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            rec->entropy = __longlong_as_double(0x7ff8000000000000ll);
+            rec->entropy_norm = rec->entropy;
+            if (host_rec) *host_rec = *rec;
+        }
+        return;
+    }
     const uint32_t nb = rec->nbins;
     const uint32_t nslabs = nb > kU32Bins ? k2_grid / 2 : k2_grid;   // see K2's two layouts
     const uint32_t j = blockIdx.x * 256 + threadIdx.x;
@@ -349,13 +359,13 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, k2_histogram<K>, keys, n, flip, head, nvec,
-                                           (const DevFeatures*)s.rec, s.slabs);
+                                           (const DevFeatures*)s.rec, s.slabs, (int)s.skip_sorted);
         if (e != cudaSuccess) return e;
     }
     {
         TraceScope ts("features_entropy", 0, st);
         k3_entropy<<<kEntropyBlocks, 256, 0, st>>>(s.slabs, g2, n, s.rec, s.hist, s.ent_partials,
-                                                   s.host_rec, s.host_hist);
+                                                   s.host_rec, s.host_hist, (int)s.skip_sorted);
     }
     return cudaGetLastError();
 }

@@ -57,6 +57,8 @@ struct FeatureScratch {
     // Optional pinned host mirrors that K3 fills (null: device copies only).
     DevFeatures* host_rec = nullptr;
     unsigned long long* host_hist = nullptr;   // nbins counts
+    // K2 and K3 skip an input K1 found in order (no histogram; entropy NaN).
+    bool skip_sorted = false;
 };
 uint32_t k1_blocks(uint64_t n, int sms);
 size_t features_scratch_bytes(int sms);

@@ -262,3 +262,34 @@ def test_sort_host_pipeline(ahs, ctx):
         assert len(picks) == len(arrays)
         for a, o in zip(arrays, host_out):
             assert np.array_equal(o.numpy().view(np.uint32), np.sort(a))
+
+
+def test_sorted_input_skips_histogram_only_when_identity(ahs, orc):
+    """Under GB300 an input in order is returned as it is without its
+    histogram (entropy NaN); under PAPER, or when a strategy is forced, the
+    histogram is built and the result is the oracle's."""
+    import torch
+    a = np.sort(_gen("uniform_full", 300_001, np.uint32, 5))
+    g = ahs.Context(0, select_mode=ahs.AHS_SEL_GB300)
+    p = ahs.Context(0, select_mode=ahs.AHS_SEL_PAPER)
+    try:
+        r = g.sort(dev(a), key_type=ahs.AHS_U32)
+        torch.cuda.synchronize()
+        assert r.strategy == ahs.AHS_IDENTITY
+        assert math.isnan(r.info.features.entropy_bits) and math.isnan(r.info.features.entropy_norm)
+        assert r.info.features.descents == 0
+        assert np.array_equal(host(r.keys, np.uint32), a)
+        of = orc.features(a)
+        rp = p.sort(dev(a), key_type=ahs.AHS_U32)
+        torch.cuda.synchronize()
+        assert math.isclose(rp.info.features.entropy_bits, of.entropy, rel_tol=ENT_REL, abs_tol=ENT_ABS)
+        assert np.array_equal(host(rp.keys, np.uint32), a)
+        for force in (ahs.AHS_GENERAL, ahs.AHS_RADIX):
+            rf = g.sort(dev(a), force=force, key_type=ahs.AHS_U32)
+            torch.cuda.synchronize()
+            assert math.isclose(rf.info.features.entropy_bits, of.entropy, rel_tol=ENT_REL,
+                                abs_tol=ENT_ABS)
+            assert np.array_equal(host(rf.keys, np.uint32), a)
+    finally:
+        g.close()
+        p.close()
