@@ -1,7 +1,7 @@
 /* Adaptive Hybrid Sort (arXiv 2506.20677): CPU oracle — TEST INFRASTRUCTURE ONLY.
  *
  * A plain, slow, single-threaded statement of what the method computes, used
- * to judge the GPU library.  It shares no code, header, table or constant with
+ * to check the GPU library against.  It shares no code, header, table or constant with
  * the library under paper_2506_20677_gb300/, and the library never loads it.
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
  * reference legs may load or execute it.
