@@ -120,7 +120,7 @@ cudaError_t finish_t(const FinalBucket* d_lists[kBucketClasses], const uint32_t 
         e = finish_class<K, VALS, 256, 16>(d_lists[3], counts[3], keys[3], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
-        e = finish_class<K, VALS, 288, 16>(d_lists[4], counts[4], keys[4], b0, b1, b2, out, vb0,
+        e = finish_class<K, VALS, 256, 18>(d_lists[4], counts[4], keys[4], b0, b1, b2, out, vb0,
                                            vb1, vb2, vout, flip, st);
     if (e == cudaSuccess)
         e = finish_class<K, VALS, 384, 16>(d_lists[5], counts[5], keys[5], b0, b1, b2, out, vb0,

@@ -9,7 +9,7 @@
 namespace ahs {
 
 // Largest bucket one CTA sorts in shared memory, and the size classes of the
-// bucket kernels (threads x keys: 128x8, 256x8, 192x16, 256x16, 288x16,
+// bucket kernels (threads x keys: 128x8, 256x8, 192x16, 256x16, 256x18,
 // 384x16, 512x16).  Classes at most 1.5x apart keep a bucket's CTA at least
 // two thirds full; the 4,608 class catches histogram bins of just over
 // 4,096 keys (2^28 keys in 2^16 bins).
