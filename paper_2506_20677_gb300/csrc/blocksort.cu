@@ -26,18 +26,20 @@ blocksort_single(const K* keys_in, K* keys_out, const uint32_t* vals_in, uint32_
 // One CTA per final bucket: sort src[begin, begin+size) into out (sorted
 // buckets), or copy it (buckets whose keys are all equal need no pass).  The
 // source is buffer 0 (temporary), 1 (the output itself) or 2 (the input).
-// Resident CTAs per SM each keys-only uint32 bucket class is compiled for
-// (its registers then still hold the keys without spilling); wider keys and
-// payloads leave the register budget to the compiler.
-template <typename K, bool VALS, int T>
+// Resident CTAs per SM each keys-only uint32 bucket class is compiled for,
+// as measured: 256 x 16 at five CTAs (a few spilled bytes) beat four by 4 %,
+// while 256 x 18 lost 9 % at five.  Wider keys and payloads leave the
+// register budget to the compiler.
+template <typename K, bool VALS, int T, int IPT>
 struct BucketMinBlocks {
-    static constexpr int kN = (sizeof(K) == 4 && !VALS)
-                                  ? (T <= 128 ? 8 : (T <= 192 ? 5 : (T <= 256 ? 4 : (T <= 384 ? 3 : 2))))
-                                  : 1;
+    static constexpr int kN =
+        (sizeof(K) == 4 && !VALS)
+            ? (T <= 128 ? 8 : (T <= 192 ? 5 : (T <= 256 ? (IPT <= 16 ? 5 : 4) : (T <= 384 ? 3 : 2))))
+            : 1;
 };
 
 template <typename K, bool VALS, int T, int IPT>
-__global__ void __launch_bounds__(T, BucketMinBlocks<K, VALS, T>::kN)
+__global__ void __launch_bounds__(T, BucketMinBlocks<K, VALS, T, IPT>::kN)
 bucket_finish(const FinalBucket* __restrict__ list, const K* buf0, const K* buf1, const K* buf2,
               K* out, const uint32_t* vbuf0, const uint32_t* vbuf1, const uint32_t* vbuf2,
               uint32_t* vout, K flip) {
