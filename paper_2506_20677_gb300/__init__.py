@@ -214,6 +214,11 @@ class Context:
         self.device = device
 
     def close(self):
+        hp = getattr(self, "_hp", None)
+        if hp is not None:   # sort_host's streams may still use its buffers
+            for k in ("sort", "out", "in"):
+                hp[k].synchronize()
+            self._hp = None
         if self.handle:
             lib.ahs_destroy(self.handle)
             self.handle = ctypes.c_void_p()
@@ -279,13 +284,19 @@ class Context:
         return SortResult(out, vals_out, info.strategy, info)
 
     def sort_host(self, host_keys, host_out, key_type=None, force: int = AHS_AUTO,
-                  stream=None, device_buffers=None):
+                  stream=None, device_buffers=None, wait: bool = True):
         """Sort a sequence of host arrays (pinned, for asynchronous copies) into
         the matching host outputs, overlapping the copy of array i + 1 to the
         device and of array i - 1 back with the sort of array i.  Each array is
         sorted on its own by ahs_sort.  device_buffers: optional pair of
         (keys, out) device tensor pairs large enough for every array (reused
-        across calls).  Returns the strategies used."""
+        across calls).  The copy and sort streams and the buffers' events
+        persist in the context, so consecutive calls also overlap: the next
+        call's first copy in waits only for the buffer it reuses.
+
+        wait=True: `stream` (default: the current stream) waits for the whole
+        call.  wait=False: it waits only for this call's start; call
+        wait_host(stream) before reading host_out.  Returns the strategies."""
         import torch
         if len(host_out) != len(host_keys) or any(
                 h.dtype != host_keys[0].dtype or o.dtype != h.dtype or o.numel() != h.numel()
@@ -293,57 +304,85 @@ class Context:
             raise AhsError(AHS_ERR_INVALID_ARG, "sort_host: one dtype, matching output sizes")
         dev = torch.device("cuda", self.device)
         cap = max((h.numel() for h in host_keys), default=0)
-        if device_buffers is None:
-            proto = host_keys[0] if host_keys else torch.empty(0, dtype=torch.int32)
-            device_buffers = [(torch.empty(cap, dtype=proto.dtype, device=dev),
-                               torch.empty(cap, dtype=proto.dtype, device=dev)) for _ in range(2)]
-        # Private streams for the sorts and both copy directions; the caller's
-        # stream orders them against its own work at entry and exit.
         caller = stream if stream is not None else torch.cuda.current_stream(dev)
-        sort_st = torch.cuda.Stream(dev)
-        in_st = torch.cuda.Stream(dev)
-        out_st = torch.cuda.Stream(dev)
-        sort_st.wait_stream(caller)
-        in_st.wait_stream(caller)
-        out_st.wait_stream(caller)
-        loaded = [torch.cuda.Event() for _ in range(2)]
-        sorted_ev = [torch.cuda.Event() for _ in range(2)]
-        freed = [torch.cuda.Event() for _ in range(2)]     # buffer's output copied back
-        consumed = [torch.cuda.Event() for _ in range(2)]  # buffer's input read by the sort
+        hp = self._host_pipe(dev, host_keys[0].dtype if host_keys else torch.int32, cap,
+                             device_buffers)
+        # The caller's earlier work (which may produce the host inputs) comes first.
+        entry = torch.cuda.Event()
+        entry.record(caller)
+        hp["in"].wait_event(entry)
+        hp["sort"].wait_event(entry)
+        bufs, ev = hp["bufs"], hp["ev"]
+        first = hp["turn"]
         picks = []
 
         def load(i):
-            b = i % 2
-            with torch.cuda.stream(in_st):
-                if i >= 2:
-                    in_st.wait_event(consumed[b])
-                k = device_buffers[b][0][: host_keys[i].numel()]
+            b = (first + i) % 2
+            with torch.cuda.stream(hp["in"]):
+                hp["in"].wait_event(ev["consumed"][b])    # the last sort that read buffer b
+                k = bufs[b][0][: host_keys[i].numel()]
                 k.copy_(host_keys[i], non_blocking=True)
-                loaded[b].record(in_st)
+                ev["loaded"][b].record(hp["in"])
 
         if host_keys:
             load(0)
         for i in range(len(host_keys)):
-            b = i % 2
+            b = (first + i) % 2
             if i + 1 < len(host_keys):
                 load(i + 1)
             m = host_keys[i].numel()
-            k, o = device_buffers[b][0][:m], device_buffers[b][1][:m]
-            sort_st.wait_event(loaded[b])
-            if i >= 2:
-                sort_st.wait_event(freed[b])
-            r = self.sort(k, out=o, force=force, key_type=key_type, stream=sort_st)
-            consumed[b].record(sort_st)
-            sorted_ev[b].record(sort_st)
+            k, o = bufs[b][0][:m], bufs[b][1][:m]
+            hp["sort"].wait_event(ev["loaded"][b])
+            hp["sort"].wait_event(ev["freed"][b])       # the last copy out of buffer b
+            r = self.sort(k, out=o, force=force, key_type=key_type, stream=hp["sort"])
+            ev["consumed"][b].record(hp["sort"])
             picks.append(r.strategy)
-            with torch.cuda.stream(out_st):
-                out_st.wait_event(sorted_ev[b])
+            with torch.cuda.stream(hp["out"]):
+                hp["out"].wait_event(ev["consumed"][b])
                 host_out[i].copy_(o, non_blocking=True)
-                freed[b].record(out_st)
-        caller.wait_stream(sort_st)
-        caller.wait_stream(out_st)
-        caller.wait_stream(in_st)
+                ev["freed"][b].record(hp["out"])
+        hp["turn"] = (first + len(host_keys)) % 2
+        if wait:
+            self.wait_host(caller)
         return picks
+
+    def wait_host(self, stream=None):
+        """Make `stream` (default: the current stream) wait for every
+        sort_host call issued so far."""
+        import torch
+        hp = getattr(self, "_hp", None)
+        if hp is None:
+            return
+        caller = stream if stream is not None else torch.cuda.current_stream(hp["dev"])
+        for k in ("sort", "out", "in"):
+            caller.wait_stream(hp[k])
+
+    def _host_pipe(self, dev, dtype, cap, device_buffers):
+        """The persistent streams, per-buffer events and device buffers of sort_host."""
+        import torch
+        hp = getattr(self, "_hp", None)
+        if device_buffers is not None:
+            bufs = device_buffers
+        elif hp is not None and hp["bufs"][0][0].dtype == dtype and hp["bufs"][0][0].numel() >= cap:
+            bufs = hp["bufs"]
+        else:
+            bufs = [(torch.empty(cap, dtype=dtype, device=dev), torch.empty(cap, dtype=dtype, device=dev))
+                    for _ in range(2)]
+        if hp is None:
+            hp = {"dev": dev, "turn": 0,
+                  "sort": torch.cuda.Stream(dev), "in": torch.cuda.Stream(dev),
+                  "out": torch.cuda.Stream(dev),
+                  "ev": {k: [torch.cuda.Event(), torch.cuda.Event()]
+                         for k in ("loaded", "consumed", "freed")},
+                  "bufs": bufs}
+            self._hp = hp
+        elif not (hp["bufs"] is bufs or all(
+                x.data_ptr() == y.data_ptr() for p, q in zip(hp["bufs"], bufs) for x, y in zip(p, q))):
+            # New buffers: the old ones may still be in use by earlier calls.
+            for k in ("sort", "out", "in"):
+                hp[k].synchronize()
+            hp["bufs"] = bufs
+        return hp
 
     def sort_batch(self, keys, seg_offsets, out=None, vals=None, vals_out=None, key_type=None,
                    stream=None):

@@ -256,12 +256,24 @@ def test_sort_host_pipeline(ahs, ctx):
     arrays[3] = rng.integers(0, 4000, size=sizes[3], dtype=np.uint32)
     host_in = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in arrays]
     host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-    for _ in range(2):   # the second call reuses nothing from the first
+    for _ in range(2):   # the second call reuses the first one's streams and buffers
         picks = ctx.sort_host(host_in, host_out, key_type=ahs.AHS_U32)
         torch.cuda.synchronize()
         assert len(picks) == len(arrays)
         for a, o in zip(arrays, host_out):
             assert np.array_equal(o.numpy().view(np.uint32), np.sort(a))
+    # Back-to-back calls that do not wait overlap; outputs are complete after
+    # wait_host, each call's into its own outputs.
+    outs = [[torch.empty_like(h).pin_memory() for h in host_in] for _ in range(3)]
+    for o in outs:
+        for t in o:
+            t.fill_(-1)
+        ctx.sort_host(host_in, o, key_type=ahs.AHS_U32, wait=False)
+    ctx.wait_host()
+    torch.cuda.synchronize()
+    for o in outs:
+        for a, t in zip(arrays, o):
+            assert np.array_equal(t.numpy().view(np.uint32), np.sort(a))
 
 
 def test_sorted_input_skips_histogram_only_when_identity(ahs, orc):
