@@ -354,7 +354,7 @@ def run_ours(args, world, rank, local):
 
     batched = served = None
     if not args.no_extras:
-        batched = run_batched(ctx, args.batch_segments, 3)
+        batched = run_batched(ctx, args.batch_segments, 10)
         served = run_served(local, args.serve_load, args.serve_seconds)
 
     cpu = None
@@ -417,7 +417,9 @@ def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    times_sorted = sorted(times)
     res = {"segments": n_seg, "keys": total, "batched_ms_p50": round(statistics.median(times), 3),
+           "batched_ms_p99": round(times_sorted[min(len(times_sorted) - 1, int(0.99 * len(times_sorted)))], 3),
            "batched_gkeys_s": round(total / (statistics.median(times) / 1e3) / 1e9, 3),
            "seg_per_strategy": {ahs.STRATEGY_NAMES[i]: int(info.seg_per_strategy[i]) for i in range(1, 6)}}
     if per_array:
@@ -584,7 +586,7 @@ def run_case(args, local):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=1 << 28, help="keys per array (default 2^28)")
