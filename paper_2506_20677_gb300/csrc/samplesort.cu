@@ -792,40 +792,59 @@ struct ClassLists {
 };
 
 
-// Upload a final-bucket list to the auxiliary buffer and run the bucket
-// sorts (one launch per size class); synchronises before returning so the
-// pinned staging can be reused.
-ahs_status finish_buckets(ahs_ctx* ctx, const std::vector<FinalBucket>& finals, const void* ktmp,
-                          const void* kout, const void* kin, const uint32_t* vtmp, uint32_t* vout,
-                          const uint32_t* vin, KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
-    // Entries per class (a large copy, the equality bucket of a heavy key, is
-    // split so that many CTAs share it), then the lists written in place.
-    size_t per[kBucketClasses] = {};
-    for (const FinalBucket& f : finals)
-        per[f.sort ? bucket_class(f.size) : 0] += (!f.sort && f.size > kCopyChunk) ? ceil_div(f.size, kCopyChunk) : 1;
+// Final buckets sorted into the size classes as they are found (a large
+// copy, the equality bucket of a heavy key, is split so that many CTAs share
+// it), so the upload is one copy per class.
+struct FinalSet {
+    std::vector<FinalBucket> cls[kBucketClasses];
+    uint64_t keys[kBucketClasses] = {};
+    uint32_t sorted = 0;
+    void reserve(size_t n) {
+        cls[0].reserve(n / 4 + 64);
+        for (int k = 1; k < kBucketClasses; ++k) cls[k].reserve(n / 2 + 16);
+    }
+    void add(const FinalBucket& f) {
+        if (!f.sort && f.size > kCopyChunk) {
+            for (uint32_t o = 0; o < f.size; o += kCopyChunk)
+                cls[0].push_back(final_bucket(f.begin + o, std::min(kCopyChunk, f.size - o), f.where, false));
+            keys[0] += f.size;
+            return;
+        }
+        const int k = f.sort ? (int)bucket_class(f.size) : 0;
+        cls[k].push_back(f);
+        keys[k] += f.size;
+        sorted += f.sort;
+    }
+};
+
+// Upload a final-bucket set to the auxiliary buffer and run the bucket sorts
+// (one launch per size class); synchronises before returning so the pinned
+// staging can be reused.
+ahs_status finish_buckets(ahs_ctx* ctx, const FinalSet& fs, const void* ktmp, const void* kout,
+                          const void* kin, const uint32_t* vtmp, uint32_t* vout, const uint32_t* vin,
+                          KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
     size_t nf = 0, at[kBucketClasses];
+    uint32_t counts[kBucketClasses];
     for (int k = 0; k < kBucketClasses; ++k) {
         at[k] = nf;
-        nf += per[k];
+        counts[k] = (uint32_t)fs.cls[k].size();
+        nf += counts[k];
     }
-    if (sorted) *sorted = 0;
+    if (sorted) *sorted = fs.sorted;
     if (nf == 0) return AHS_OK;
     ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
     if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
     if (rc != AHS_OK) return rc;
     FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
     FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
-    ClassLists cl;
-    cl.cap = nf;
-    for (int k = 0; k < kBucketClasses; ++k) cl.region[k] = hf + at[k];
-    for (const FinalBucket& f : finals) cl.add(f);
-    if (cl.overflow) return AHS_ERR_CUDA;
-    if (sorted) *sorted = cl.sorted;
     const FinalBucket* lists[kBucketClasses];
-    for (int k = 0; k < kBucketClasses; ++k) lists[k] = df + at[k];
+    for (int k = 0; k < kBucketClasses; ++k) {
+        std::memcpy(hf + at[k], fs.cls[k].data(), counts[k] * sizeof(FinalBucket));
+        lists[k] = df + at[k];
+    }
     cudaError_t e = launch_transfer(df, hf, nf * sizeof(FinalBucket), st);
     if (e == cudaSuccess)
-        e = launch_bucket_finish(lists, cl.count, cl.keys, ktmp, kout, kin, const_cast<void*>(kout),
+        e = launch_bucket_finish(lists, counts, fs.keys, ktmp, kout, kin, const_cast<void*>(kout),
                                  vtmp, vout, vin, vout, kd, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
@@ -844,14 +863,14 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
     cudaError_t e = set_attrs<K, VALS>();
     if (e != cudaSuccess) return cuda_status(ctx, e);
 
-    std::vector<FinalBucket> finals;
+    FinalSet finals;
     // Buckets hold a CTA's capacity / 2 keys on average: reserve for that.
     finals.reserve(extra.size() + segs.size() + 2 * (n_total / (kBucketCap / 2)) + 64);
     for (const SegRange& x : extra)
-        finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
+        finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
     std::vector<SegRange> open;
     for (const SegRange& x : segs) {
-        if (x.size <= kBucketCap) finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
+        if (x.size <= kBucketCap) finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
         else open.push_back(x);
     }
     Level L;
@@ -890,9 +909,9 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
                 const unsigned long long b0 = L.segs[s].begin + base[(size_t)s * kCols + j];
                 const bool equal = (j & 1u) != 0;
                 if (equal || sz == 1) {
-                    if (where == 0) finals.push_back(final_bucket(b0, sz, where, false));   // copy to output
+                    if (where == 0) finals.add(final_bucket(b0, sz, where, false));   // copy to output
                 } else if (sz <= kBucketCap) {
-                    finals.push_back(final_bucket(b0, sz, where, true));
+                    finals.add(final_bucket(b0, sz, where, true));
                 } else {
                     next.push_back({b0, sz, 0});
                 }
@@ -1389,10 +1408,10 @@ ahs_status run_segmented_radix(ahs_ctx* ctx, const void* kin, void* kout, const 
 ahs_status run_small_segments(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,
                               uint32_t* vout, const std::vector<SegRange>& sort_segs,
                               const std::vector<SegRange>& copy_segs, KeyDesc kd, cudaStream_t st) {
-    std::vector<FinalBucket> finals;
+    FinalSet finals;
     finals.reserve(sort_segs.size() + copy_segs.size());
-    for (const SegRange& x : sort_segs) finals.push_back(final_bucket(x.begin, x.size, 2, x.size > 1));
-    for (const SegRange& x : copy_segs) finals.push_back(final_bucket(x.begin, x.size, 2, false));
+    for (const SegRange& x : sort_segs) finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
+    for (const SegRange& x : copy_segs) finals.add(final_bucket(x.begin, x.size, 2, false));
     // No temporary buffer is involved: every bucket reads kin and writes kout.
     return finish_buckets(ctx, finals, kout, kout, kin, vout, vout, vin, kd, st, nullptr);
 }
