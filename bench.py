@@ -43,6 +43,23 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
     return table.get(kernel, 0.0)
 
 
+def kernel_table(kt, peak, w: int = 4, v: int = 0):
+    """Per kernel: launches, total ms, share of kernel time and, where the
+    kernel's algorithmic bytes per key are known, its GB/s over all launches
+    and that as a fraction of `peak` (the per-pass roofline)."""
+    total = sum(x[1] for x in kt.values()) or 1.0
+    out = {}
+    for k, (c, m, items) in sorted(kt.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches": c, "ms": round(m, 3), "share": round(m / total, 4)}
+        per = algo_bytes_per_item(k, w, v)
+        if per and items and m > 0:
+            gbs = per * items / (m / 1e3) / 1e9
+            e["gbs"] = round(gbs, 1)
+            e["frac"] = round(gbs / peak, 4) if peak else None
+        out[k] = e
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -316,8 +333,7 @@ def run_ours(args, world, rank, local):
     items_per_launch = items_k / launches
     bytes_per_launch = algo_bytes_per_item(dom, 4, 0) * items_per_launch
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    kernels = {k: {"launches": c, "ms": round(m, 3), "share": round(m / sum(x[1] for x in kt.values()), 4)}
-               for k, (c, m, _) in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+    kernels = kernel_table(kt, peak)
 
     # End to end through the public API with host buffers: every step copies
     # each input from pinned host memory to the device, sorts it and copies the
