@@ -104,3 +104,21 @@ def test_entropy_invariant_under_shift(orc):
 def test_rejects_non_integer(orc):
     with pytest.raises(TypeError):
         orc.features(np.zeros(4, dtype=np.float32))
+
+
+def test_zipf_sample_entropy_near_population(orc):
+    """Config 2b draws Zipf(1.1) over 1,024 distinct values: the exact
+    per-value entropy of a 2^22-key sample lies near the population's
+    H = -sum p_r log2 p_r, p_r = r^-1.1 / sum_j j^-1.1 (sampling error about
+    1e-3 bits here, plug-in bias about 2e-4)."""
+    from gen import host as gen
+    r = np.arange(1, 1025, dtype=np.float64)
+    p = r ** -1.1
+    p /= p.sum()
+    h_pop = float(-(p * np.log2(p)).sum())
+    assert abs(h_pop - 6.8214) < 1e-3            # the population value of this recipe
+    a = gen.config2("b", 1 << 22)
+    h = orc.entropy_exact(a)
+    assert abs(h - h_pop) < 5e-3
+    # The 2^16-bin feature entropy cannot exceed the exact one (bins merge values).
+    assert orc.features(a).entropy <= h + 1e-9
