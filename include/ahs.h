@@ -68,8 +68,13 @@ typedef enum {
  *  GB300:    the same chain with k_t = 65,536 (the largest range whose counting
  *            histogram is the feature histogram itself, the analogue of Eq. 2),
  *            n_t = the one-block sort capacity, and "already in order" -> IDENTITY.
- *  MODEL:    n < 1000 -> GB300 rules; otherwise a tree ensemble evaluated on
- *            (log2 n, log2 k, h, key bytes, has payload) (Section III-H, Table IV).
+ *  MODEL:    Section III-H, Table IV.  n < 1000: the static thresholds
+ *            n <= 20 -> SMALL and k <= 500 -> COUNTING, then the GB300 rules;
+ *            n >= 1000: k == 1 or an input in order -> IDENTITY, otherwise a tree
+ *            ensemble evaluated on (log2 n, log2 k, h, key bytes, has payload),
+ *            COUNTING only for k <= 65,536 and SMALL only up to the GB300 n_t
+ *            (else GENERAL).  Without a loaded table every n takes the small-n
+ *            branch.
  *  CUSTOM:   the thresholds given in ahs_config_t.thresholds. */
 typedef enum {
     AHS_SEL_PAPER = 0, AHS_SEL_LISTING6 = 1, AHS_SEL_GB300 = 2, AHS_SEL_MODEL = 3,
@@ -194,17 +199,19 @@ ahs_status ahs_trace_collect(ahs_ctx* ctx, ahs_trace_entry_t* out, uint32_t cap,
 ahs_status ahs_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_type type,
                         void* stream, ahs_features_t* h_out);
 
-/* Feature extraction that allocates nothing.  The paper has no counterpart:
- * this serves callers that cannot call cudaMalloc when they need the state
- * vector (for instance while a stream is being captured into a CUDA graph,
- * when all device memory is reserved up front by another allocator, or on a
- * path that cannot afford the device synchronisation of cudaMalloc/cudaFree).
- * It runs the same kernels as ahs_features and returns the same result, with
- * no ahs_ctx.  Its scratch is one fixed 48 MiB device array inside the
- * library, held by every GPU that loads the library until the process exits.
+/* Feature extraction that allocates nothing.  The paper has no counterpart.
+ * It serves callers that cannot call cudaMalloc when they need the state
+ * vector: code whose device memory is all reserved up front by another
+ * allocator or pool (a framework's caching allocator holding the whole HBM),
+ * and latency-bound paths that cannot afford the device-wide synchronisation
+ * of cudaMalloc / cudaFree.  It runs the same kernels as ahs_features and
+ * returns the same result, with no ahs_ctx.  Its scratch is one fixed 48 MiB
+ * device array inside the library, held by every GPU that loads the library
+ * until the process exits.
  *  - d_keys: device keys on the current device; n <= AHS_NOALLOC_MAX_KEYS.
- *  - The first call on a device resolves the array's device address for that
- *    device; make that first call before any stream capture.
+ *  - The first call on a device (with that device current) resolves the
+ *    array's device address for that device; a failed attempt is retried by
+ *    the next call.
  *  - All calls share the one array, which keeps the previous call's contents
  *    (each call clears what must start at zero): calls that overlap on the GPU
  *    (other streams, other threads) race and must not be issued.

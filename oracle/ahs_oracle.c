@@ -187,10 +187,14 @@ int orc_insertion_sort(const void* keys, void* out, const uint32_t* vals, uint32
     return ORC_OK;
 }
 
-/* ----------------------------------------------------- Listing 2: counting sort */
+/* ------------------------------------------------- Section III-F: counting sort */
 
-/* Count[i] = #{j : A[j] - min = i}; prefix sums; then a reverse scan that places
- * A[j] at Count[A[j] - min] - 1 and decrements (stable). */
+/* Section III-F defines counting sort by the frequency of each value,
+ * Count[c] = #{j : A[j] - min = c}, and places every key by the accumulated
+ * counts of the values before it.  Written from that definition: start[c] =
+ * sum of Count[c'] over c' < c is where the first key of value min + c goes,
+ * and the keys of one value take start[c], start[c] + 1, ... in input order,
+ * so the order is stable. */
 int orc_counting_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_out,
                       uint64_t n, int t) {
     if (!valid_type(t)) return ORC_EINVAL;
@@ -201,20 +205,23 @@ int orc_counting_sort(const void* keys, void* out, const uint32_t* vals, uint32_
     for (uint64_t i = 0; i < n; ++i) { if (a[i] < mn) mn = a[i]; if (a[i] > mx) mx = a[i]; }
     uval_t range = (uval_t)(mx - mn) + 1;
     if (range > ((uval_t)1 << 28)) { free(a); return ORC_ERANGE; }
-    uint64_t* count = (uint64_t*)calloc((size_t)range, sizeof(uint64_t));
+    uint64_t* start = (uint64_t*)calloc((size_t)range, sizeof(uint64_t));
     val_t* o = (val_t*)malloc(n * sizeof(val_t));
-    if (!count || !o) { free(a); free(count); free(o); return ORC_ENOMEM; }
-    for (uint64_t i = 0; i < n; ++i) count[(uint64_t)(a[i] - mn)] += 1;
-    for (uint64_t i = 1; i < (uint64_t)range; ++i) count[i] += count[i - 1];
-    for (uint64_t i = n; i-- > 0;) {
-        uint64_t c = (uint64_t)(a[i] - mn);
-        uint64_t pos = count[c] - 1;
+    if (!start || !o) { free(a); free(start); free(o); return ORC_ENOMEM; }
+    for (uint64_t i = 0; i < n; ++i) start[(uint64_t)(a[i] - mn)] += 1;   /* Count[c] */
+    uint64_t before = 0;                     /* keys of smaller values */
+    for (uint64_t c = 0; c < (uint64_t)range; ++c) {
+        uint64_t count = start[c];
+        start[c] = before;
+        before += count;
+    }
+    for (uint64_t i = 0; i < n; ++i) {       /* input order: equal keys stay in order */
+        uint64_t pos = start[(uint64_t)(a[i] - mn)]++;
         o[pos] = a[i];
         if (vals) vals_out[pos] = vals[i];
-        count[c] -= 1;
     }
     store_all(out, o, n, t);
-    free(a); free(count); free(o);
+    free(a); free(start); free(o);
     return ORC_OK;
 }
 
@@ -462,9 +469,18 @@ int orc_model_predict(const orc_model* m, const double* x) {
 int orc_select_model(const orc_features_t* f, const orc_model* m, uint32_t key_bytes, int payload,
                      const orc_fsm_t* rules, uint64_t small_capacity) {
     int s;
+    uval_t k = (uval_t)f->span + 1;
     if (f->n < 1000 || !m) {
-        s = orc_select(f, rules);
-    } else if (f->n <= 1 || f->span == 0 || (rules->sorted_identity && f->descents == 0)) {
+        /* Section III-H, Table IV: below n = 1000 static thresholds decide --
+         * n <= 20 insertion sort, k <= 500 counting sort -- and the profile's
+         * rules decide what those two leave. */
+        if (f->n <= 1) s = ORC_IDENTITY;
+        else if (rules->sorted_identity && f->descents == 0) s = ORC_IDENTITY;
+        else if (f->n <= 20) s = ORC_SMALL;
+        else if (f->span == 0) s = ORC_IDENTITY;
+        else if (k <= 500) s = ORC_COUNTING;
+        else s = orc_select(f, rules);
+    } else if (f->span == 0 || (rules->sorted_identity && f->descents == 0)) {
         s = ORC_IDENTITY;
     } else {
         double x[5];
@@ -474,7 +490,7 @@ int orc_select_model(const orc_features_t* f, const orc_model* m, uint32_t key_b
         x[3] = (double)key_bytes;
         x[4] = payload ? 1.0 : 0.0;
         s = orc_model_predict(m, x);
-        if (s == ORC_COUNTING && f->span > 65535) s = ORC_GENERAL;
+        if (s == ORC_COUNTING && k > 65536) s = ORC_GENERAL;
         if (s == ORC_SMALL && f->n > rules->n_t) s = ORC_GENERAL;
         if (s < ORC_IDENTITY || s > ORC_GENERAL) s = ORC_GENERAL;
     }

@@ -85,9 +85,12 @@ typedef struct orc_model orc_model;
 orc_model* orc_model_load(const char* path);
 void orc_model_free(orc_model* m);
 int orc_model_predict(const orc_model* m, const double* x);
-/* Table IV: static rules (the thresholds in `rules`) below n = 1000, the model
- * above; counting only for k <= 2^16 and the one-block sort only up to
- * n_t and small_capacity, otherwise the general path. */
+/* Section III-H / Table IV: below n = 1000 the static thresholds (n <= 20
+ * insertion, k <= 500 counting) and then the profile's rules (`rules`); from
+ * n = 1000 the model, after the rules' identity cases (k == 1, an ordered input
+ * under a profile that returns it as it is).  Counting only for k <= 2^16 and
+ * the one-block sort only up to n_t and small_capacity, otherwise the general
+ * path. */
 int orc_select_model(const orc_features_t* f, const orc_model* m, uint32_t key_bytes, int payload,
                      const orc_fsm_t* rules, uint64_t small_capacity);
 

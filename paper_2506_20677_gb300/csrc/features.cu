@@ -387,24 +387,20 @@ size_t features_scratch_bytes(int sms) {
 
 cudaError_t launch_features(const void* keys, uint64_t n, KeyDesc kd, const FeatureScratch& s,
                             int sms, cudaStream_t st) {
-    static bool attr_set[2] = {false, false};
+    // The dynamic shared-memory limit is a per-device attribute of the kernel:
+    // set it on every call (a cheap host call) so that every device, and every
+    // thread that launches, finds it set.
     if (kd.bytes == 4) {
-        if (!attr_set[0]) {
-            cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint32_t>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kHistSmemBytes);
-            if (e != cudaSuccess) return e;
-            attr_set[0] = true;
-        }
-        return features_t<uint32_t>(keys, n, (uint32_t)kd.flip, s, sms, st);
-    }
-    if (!attr_set[1]) {
-        cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint64_t>,
+        cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint32_t>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kHistSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set[1] = true;
+        return features_t<uint32_t>(keys, n, (uint32_t)kd.flip, s, sms, st);
     }
+    cudaError_t e = cudaFuncSetAttribute(k2_histogram<uint64_t>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kHistSmemBytes);
+    if (e != cudaSuccess) return e;
     return features_t<uint64_t>(keys, n, kd.flip, s, sms, st);
 }
 

@@ -1,16 +1,16 @@
 // Feature extraction for callers that cannot allocate device memory.
 //
 // Some callers may not call cudaMalloc at the point where they need the
-// features of an array: code running while a stream is being captured into a
-// CUDA graph (an allocation there breaks the capture), loops whose device
-// memory is fully reserved up front by another allocator or pool, and
-// latency-bound paths that cannot afford the device-wide synchronisation of
-// cudaMalloc / cudaFree.  ahs_features_noalloc serves them: it runs the same
-// three feature kernels as ahs_features, but its scratch lives in one
-// file-scope device array of fixed size (kNoAllocScratchBytes) that every GPU
-// holds from the moment the library's module is loaded there until the
-// process exits.  It needs no ahs_ctx, allocates nothing, and the caller
-// passes the input and receives the result on the host.
+// features of an array: loops whose device memory is fully reserved up front
+// by another allocator or pool (a framework's caching allocator that holds all
+// of HBM), and latency-bound paths that cannot afford the device-wide
+// synchronisation that cudaMalloc / cudaFree imply.  ahs_features_noalloc
+// serves them: it runs the same three feature kernels as ahs_features, but its
+// scratch lives in one file-scope device array of fixed size
+// (kNoAllocScratchBytes) that every GPU holds from the moment the library's
+// module is loaded there until the process exits.  It needs no ahs_ctx,
+// allocates nothing, and the caller passes the input and receives the result
+// on the host.
 #include <cstring>
 #include <mutex>
 
@@ -38,7 +38,9 @@ DeviceSetup g_setup[kMaxDevices];
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Once per device, with that device current: resolve the scratch address and
-// check that this device's feature kernels fit in it.
+// check that this device's feature kernels fit in it.  Only a definite answer
+// is kept (the address, or "this device has too many SMs"); a failed CUDA call
+// is returned and retried by the next call.
 ahs_status setup_device(int dev, DeviceSetup** out) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     DeviceSetup& s = g_setup[dev];
@@ -48,9 +50,11 @@ ahs_status setup_device(int dev, DeviceSetup** out) {
         int sms = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) {
-            s.status = e == cudaErrorMemoryAllocation ? AHS_ERR_OOM : AHS_ERR_CUDA;
-        } else if (a256(sizeof(ahs::DevFeatures)) + ahs::features_scratch_bytes(sms) >
-                   kNoAllocScratchBytes) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? AHS_ERR_OOM : AHS_ERR_CUDA;
+        }
+        if (a256(sizeof(ahs::DevFeatures)) + ahs::features_scratch_bytes(sms) >
+            kNoAllocScratchBytes) {
             s.status = AHS_ERR_RANGE;   // more SMs than the fixed scratch was sized for
         } else {
             s.status = AHS_OK;

@@ -287,13 +287,11 @@ cudaError_t radix_t(const void* kin_v, void* kout_v, const uint32_t* vin, uint32
             kin, n, mn, flip, head, nvec, pd, rs.digit_hist, dbase, rec);
     }
 
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(onesweep_pass<K, VALS, T, IPT, MINB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // A per-device attribute of the kernel: set on every call, for every
+    // device and launching thread.
+    e = cudaFuncSetAttribute(onesweep_pass<K, VALS, T, IPT, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    if (e != cudaSuccess) return e;
 
     // Buffer schedule: the last pass writes kout.  When sorting in place with
     // an odd pass count, first move the keys into the temporary buffer.

@@ -138,13 +138,21 @@ ahs_strategy select_model(const TreeModel& m, const ahs_features_t& f, uint32_t 
                           int32_t has_payload) {
     ahs_thresholds_t t;
     profile_thresholds(AHS_SEL_GB300, &t);
-    // Table IV: static rules below n = 1000, the learned model above.
-    if (f.n < 1000 || !m.loaded()) return select_fsm(f, t);
-    if (f.n <= 1 || f.span == 0 || (t.sorted_identity && f.descents == 0)) return AHS_IDENTITY;
+    const bool ordered = t.sorted_identity && f.descents == 0;
+    if (f.n < kModelMinN || !m.loaded()) {
+        // Table IV's static thresholds for small inputs (insertion sort up to
+        // n = 20, counting sort up to k = 500), the GB300 chain after them.
+        if (f.n <= 1 || ordered) return AHS_IDENTITY;
+        if (f.n <= 20) return AHS_SMALL;
+        if (f.span == 0) return AHS_IDENTITY;
+        if (f.span < kModelSmallCountingK) return AHS_COUNTING;   // k = span + 1 <= 500
+        return select_fsm(f, t);
+    }
+    if (f.span == 0 || ordered) return AHS_IDENTITY;
     double x[kModelFeatures];
     model_features(f, key_bytes, has_payload, x);
     int s = m.predict(x);
-    if (s == AHS_COUNTING && f.span > 65535) s = AHS_GENERAL;   // counting needs k <= 2^16
+    if (s == AHS_COUNTING && f.span >= kMaxBinsCounting) s = AHS_GENERAL;   // k <= 2^16 only
     if (s == AHS_SMALL && f.n > t.n_t) s = AHS_GENERAL;
     if (s < AHS_IDENTITY || s > AHS_GENERAL) s = AHS_GENERAL;
     return (ahs_strategy)s;

@@ -12,6 +12,12 @@ namespace ahs {
 // shared memory (every key type, with or without payload, fits).
 constexpr uint64_t kGb300SmallCutoff = 4096;
 constexpr int kModelFeatures = 5;
+// Section III-H / Table IV: the learned model decides from n = 1000 on; below
+// it static thresholds do, counting sort for k <= 500 among them.
+constexpr uint64_t kModelMinN = 1000;
+constexpr uint64_t kModelSmallCountingK = 500;
+// Counting sort reads its histogram from the feature pass: k <= 2^16.
+constexpr uint64_t kMaxBinsCounting = 65536;
 
 ahs_status profile_thresholds(ahs_select_mode mode, ahs_thresholds_t* t);
 ahs_strategy select_fsm(const ahs_features_t& f, const ahs_thresholds_t& p);

@@ -6,6 +6,8 @@ import threading
 import numpy as np
 import pytest
 
+import oracle
+from gen import host as gen
 from gpu_util import dev, host
 
 pytestmark = pytest.mark.gpu
@@ -35,6 +37,10 @@ def _wait(ahs, ctx, ticket, timeout_ms=60000):
     return rc, res
 
 
+def _oracle_sorted(a):
+    return oracle.sort(a, profile=oracle.PAPER)[0]
+
+
 def test_mix_equals_alone_and_oracle(ahs):
     import torch
     rng = np.random.default_rng(5)
@@ -49,6 +55,11 @@ def test_mix_equals_alone_and_oracle(ahs):
             vals = rng.integers(0, 2**32, size=1024, dtype=np.uint32)
             a = vals[rng.integers(0, 1024, size=n)]
         arrays.append(a)
+    # requests shaped like the served workload: config-4 distributions (a, b,
+    # c, e of config 2), log-uniform sizes from 10^3 keys
+    lengths = gen.log_uniform_lengths(8, 55, 1, 1000, 3_000_000)
+    for j, L in enumerate(lengths):
+        arrays.append(gen.config4_segment(900_000 + j, int(L), j % 4))
     with ahs.Context(0) as ctx:
         _serve(ahs, ctx, budget=8 << 30)
         # each request alone
@@ -80,7 +91,7 @@ def test_mix_equals_alone_and_oracle(ahs):
             assert rc == ahs.AHS_OK and res.status == ahs.AHS_OK, i
             mixed = host(outs[i], np.uint32)
             assert np.array_equal(mixed, alone[i]), i
-            assert np.array_equal(mixed, np.sort(arrays[i])), i
+            assert np.array_equal(mixed, _oracle_sorted(arrays[i])), i
         st = ahs.ahs_serve_stats_t()
         ahs.check(ahs.lib.ahs_serve_stats(ctx.handle, ctypes.byref(st)), "stats")
         assert st.completed == 2 * sum(1 for a in arrays if len(a))
@@ -105,7 +116,7 @@ def test_budget_refusal_and_admission_bound(ahs):
         for t, a, o in zip(tickets, arrays, outs):
             rc, res = _wait(ahs, ctx, t)
             assert rc == ahs.AHS_OK and res.status == ahs.AHS_OK
-            assert np.array_equal(host(o, np.uint32), np.sort(a))
+            assert np.array_equal(host(o, np.uint32), _oracle_sorted(a))
         st = ahs.ahs_serve_stats_t()
         ahs.check(ahs.lib.ahs_serve_stats(ctx.handle, ctypes.byref(st)), "stats")
         assert st.peak_reserved_bytes <= budget     # the ledger never exceeded the budget

@@ -27,8 +27,18 @@ MUTATIONS = {
                           "uint64_t u = (uint64_t)(load_key(keys, i, t));")],
     "descent_non_strict": [("x > load_key(keys, i + 1, t)", "x >= load_key(keys, i + 1, t)")],
     "insertion_unstable": [("a[j - 1] > key", "a[j - 1] >= key")],
-    "counting_forward_scan": [("for (uint64_t i = n; i-- > 0;) {\n        uint64_t c",
-                               "for (uint64_t i = 0; i < n; ++i) {\n        uint64_t c")],
+    "counting_reverse_placement": [("for (uint64_t i = 0; i < n; ++i) {       /* input order",
+                                    "for (uint64_t i = n; i-- > 0;) {       /* input order")],
+    "counting_inclusive_start": [("start[c] = before;\n        before += count;",
+                                  "before += count;\n        start[c] = before - 1;")],
+    "model_rules_at_1000": [("if (f->n < 1000 || !m) {", "if (f->n <= 1000 || !m) {")],
+    "model_small_counting_strict": [("else if (k <= 500) s = ORC_COUNTING;",
+                                     "else if (k < 500) s = ORC_COUNTING;")],
+    "model_counting_clamp_off_by_one": [("if (s == ORC_COUNTING && k > 65536)",
+                                         "if (s == ORC_COUNTING && k > 65537)")],
+    "model_small_clamp_dropped": [("if (s == ORC_SMALL && f->n > rules->n_t) s = ORC_GENERAL;", "")],
+    "model_identity_after_trees": [("} else if (f->span == 0 || (rules->sorted_identity && f->descents == 0)) {\n        s = ORC_IDENTITY;\n    } else {",
+                                    "} else {")],
     "radix_digit_stride": [("(u >> (8 * digit)) & 255] += 1", "(u >> (7 * digit)) & 255] += 1"),
                            ("(u >> (8 * digit)) & 255]++", "(u >> (7 * digit)) & 255]++")],
     "radix_without_min": [("uint64_t u = (uint64_t)(a[i] - mn);\n            bucket_size",
@@ -65,6 +75,15 @@ def _pins_pass() -> bool:
             f = oracle.Features()
             f.n, f.span, f.entropy_norm, f.descents, f.nbins = int(n), int(span), float(h), int(desc), 65536
             if oracle.select(f, getattr(oracle, profile)) != NAMES[expect]:
+                return False
+        m = oracle.Model(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                      "model_policy_trees.txt"))
+        rules = oracle.Profile(4096, 65536, 10**6, sorted_identity=True)
+        for row in read_golden("model_policy.txt"):
+            n, span, h, desc, cap, expect = row
+            f = oracle.Features()
+            f.n, f.span, f.entropy_norm, f.descents, f.nbins = int(n), int(span), float(h), int(desc), 65536
+            if m.select(f, 4, False, rules, int(cap)) != NAMES[expect]:
                 return False
         for row in read_golden("radix_passes_eq4.txt"):
             if oracle.radix_passes(int(row[0]) - 1) != int(row[1]):

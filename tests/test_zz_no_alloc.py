@@ -1,17 +1,21 @@
 """ahs_features_noalloc, the feature pass for callers that cannot allocate.
 
-Callers that may not call cudaMalloc (inside stream capture, under a fixed
-up-front memory reservation, on latency-bound paths) use this entry point; its
-scratch is a fixed array inside the library.  Through the C ABI it must return
-what ahs_features returns for the same keys, on consecutive calls that reuse
-the same scratch.  This file is collected last so that a failure here does not
-hide the rest of the suite; it passes alone and after the other tests.
+Some callers cannot call cudaMalloc when they need the features: their device
+memory is all reserved up front by another allocator or pool, or they run on a
+latency-bound path that cannot afford the synchronisation cudaMalloc / cudaFree
+imply.  This entry point serves them; its scratch is a fixed array inside the
+library.  Through the C ABI it must return what ahs_features returns for the
+same keys, and what the oracle computes, on consecutive calls that reuse the
+same scratch.  This file is collected last so that a failure here does not hide
+the rest of the suite; it passes alone and after the other tests.
 """
 import ctypes
 import math
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +27,13 @@ def _same(a, b):
         (b.n, b.min_bits, b.max_bits, b.span, b.hist_shift, b.nbins, b.descents)
     assert math.isclose(a.entropy_bits, b.entropy_bits, rel_tol=ENT_REL, abs_tol=ENT_ABS)
     assert math.isclose(a.entropy_norm, b.entropy_norm, rel_tol=ENT_REL, abs_tol=ENT_ABS)
+
+
+def _same_as_oracle(a, o):
+    assert (a.n, a.min_bits, a.max_bits, a.span, a.hist_shift, a.nbins, a.descents) == \
+        (o.n, o.min_bits, o.max_bits, o.span, o.shift, o.nbins, o.descents)
+    assert math.isclose(a.entropy_bits, o.entropy, rel_tol=ENT_REL, abs_tol=ENT_ABS)
+    assert math.isclose(a.entropy_norm, o.entropy_norm, rel_tol=ENT_REL, abs_tol=ENT_ABS)
 
 
 def _raw_noalloc(ahs, t, key_type):
@@ -45,10 +56,12 @@ def test_noalloc_matches_features_on_consecutive_calls():
         for a, kt, tdt in cases:
             t = torch.from_numpy(a.view(np.int32 if a.itemsize == 4 else np.int64)).cuda()
             ref = ctx.features(t, key_type=kt)
+            orc = oracle.features(a)
             for _ in range(2):          # two calls in a row reuse the same scratch
                 rc, f = _raw_noalloc(ahs, t, kt)
                 assert rc == ahs.AHS_OK
                 _same(f, ref)
+                _same_as_oracle(f, orc)
 
 
 def test_noalloc_edge_cases():
