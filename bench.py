@@ -217,6 +217,62 @@ def oracle_sample_run(n_sample: int, seed_offset: int = 0):
     return keys_total, secs, picks
 
 
+def std_sort_context(n_sample: int):
+    """libstdc++ std::sort on the first n_sample keys of each array, one core
+    (context beside the oracle; Gkeys/s)."""
+    import oracle
+    from gen import host as gen
+    keys, secs = 0, 0.0
+    for v in VARIANTS:
+        a = gen.config2(v, n_sample)
+        t0 = time.perf_counter()
+        oracle.std_sort(a)
+        secs += time.perf_counter() - t0
+        keys += len(a)
+    return round(keys / secs / 1e9, 4)
+
+
+def _c4_oracle_worker(share, n_seg, barrier, q):
+    """One process of the all-core oracle baseline: generate this worker's
+    config-4 segments, wait for the others, then sort them with the oracle."""
+    import oracle
+    from gen import host as gen
+    lengths, types, _ = gen.config4_layout()
+    segs = [gen.config4_segment(s, int(lengths[s]), int(types[s])) for s in range(share, n_seg, q[1])]
+    oracle.lib()
+    barrier.wait()
+    t0 = time.time()
+    keys = 0
+    for a in segs:
+        oracle.sort(a, profile=oracle.PAPER)
+        keys += len(a)
+    q[0].put((t0, time.time(), keys))
+
+
+def oracle_config4_all_cores(n_seg: int):
+    """The oracle on the first n_seg segments of config 4, one segment at a
+    time per process, on every host core (processes started with spawn, after
+    the GPU is in use).  Gkeys/s = keys / wall time of the sorting phase."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_c4_oracle_worker, args=(i, n_seg, barrier, (q, cores)))
+             for i in range(cores)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    start = min(r[0] for r in res)
+    end = max(r[1] for r in res)
+    keys = sum(r[2] for r in res)
+    return {"value": round(keys / (end - start) / 1e9, 4), "unit": "Gkeys/s", "cores": cores,
+            "kind": "oracle", "sample": f"first {n_seg} segments of config 4 ({keys} keys, "
+                                        f"{end - start:.1f} s), one segment per process at a time"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -321,6 +377,11 @@ def run_ours(args, world, rank, local):
         p99 = xs[min(len(xs) - 1, int(round(0.99 * (len(xs) - 1))))]
         per_strategy[v] = {"strategy": picks[v], "ms_p50": round(p50, 4), "ms_p99": round(p99, 4),
                            "gkeys_s_p50": round(n / (p50 / 1e3) / 1e9, 3)}
+        if picks[v] == "IDENTITY":
+            per_strategy[v]["note"] = ("input found in order by the min/max pass and returned as "
+                                       "a copy (GB300 profile's presorted rule)")
+    ms_sorting = sum(statistics.median(vt[v]) for v in VARIANTS if picks[v] != "IDENTITY")
+    n_sorting = sum(1 for v in VARIANTS if picks[v] != "IDENTITY")
     kt = collections.defaultdict(lambda: [0, 0.0, 0])
     for name, items, ms, _ in trace:
         kt[name][0] += 1
@@ -368,10 +429,13 @@ def run_ours(args, world, rank, local):
     e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
     e2e_value = job_value(world, keys_per_step, args.steps, e2e_ms)
 
-    batched = served = None
+    batched = served = cfg1 = cfg3 = None
     if not args.no_extras:
+        cfg1 = run_config1(ctx, 100, stream)
+        cfg3 = run_config3(ctx, 30, stream, peak)
         batched = run_batched(ctx, args.batch_segments, 10)
-        served = run_served(local, args.serve_load, args.serve_seconds)
+        served = [run_served(local, load, args.serve_seconds)
+                  for load in args.serve_loads]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -379,7 +443,11 @@ def run_ours(args, world, rank, local):
         oracle.build()
         k, s, _ = oracle_sample_run(args.ref_sample)
         cpu = {"value": k / s / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {args.ref_sample} keys of each of the 6 arrays ({k} keys, {s:.1f} s)"}
+               "sample": f"first {args.ref_sample} keys of each of the 6 arrays ({k} keys, {s:.1f} s)",
+               "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(),
+               "std_sort_gkeys_s": std_sort_context(args.ref_sample)}
+        if not args.no_extras:
+            cpu["config4_all_cores"] = oracle_config4_all_cores(args.cpu_segments)
 
     if rank == 0:
         line = {
@@ -393,6 +461,9 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"replicas x{world}",
                        "host_cpus": f"{len(bound)} GPU-local" if bound else "unbound"},
             "per_strategy": per_strategy,
+            "sorting_arrays_gkeys_s": round(n_sorting * n / (ms_sorting / 1e3) / 1e9, 3),
+            "config1": cfg1,
+            "config3": cfg3,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_kind": peak_kind,
@@ -410,6 +481,104 @@ def run_ours(args, world, rank, local):
         }
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def percentiles(xs):
+    xs = sorted(xs)
+    return statistics.median(xs), xs[min(len(xs) - 1, int(round(0.99 * (len(xs) - 1))))]
+
+
+def timed_calls(fn, reps: int, stream):
+    """Device time of each of `reps` calls of fn(), CUDA events on `stream`."""
+    import torch
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def run_config1(ctx, reps: int, stream):
+    """Config 1: 2^20 uint32 keys uniform in [0, 255] (seed 0), AUTO pipeline
+    (features -> selector -> counting sort).  Latency-bound and L2-resident:
+    reported in microseconds with p50 / p99 over `reps` calls."""
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    from gen import device as gdev
+    keys = gdev.config1()
+    out = torch.empty_like(keys)
+    n = keys.numel()
+    call = lambda: ctx.sort(keys, out=out, key_type=ahs.AHS_U32, stream=stream)
+    for _ in range(5):
+        r = call()
+    torch.cuda.synchronize()
+    p50, p99 = percentiles(timed_calls(call, reps, stream))
+    return {"n": n, "strategy": ahs.STRATEGY_NAMES[r.strategy], "us_p50": round(1e3 * p50, 1),
+            "us_p99": round(1e3 * p99, 1), "gkeys_s_p50": round(n / (p50 / 1e3) / 1e9, 3),
+            "calls": reps, "note": "latency-bound, L2-resident (12 MiB of algorithmic traffic)"}
+
+
+def run_config3(ctx, reps: int, stream, peak: float):
+    """Config 3: 2^27 uint64 timestamp-ramp keys (5% replaced by uniform draws
+    over the ramp's range) with a uint32 payload = original index, forced
+    RADIX (stable LSD digit passes).  p50 / p99 and per-kernel fractions of
+    the HBM peak; the path's fraction is against the minimum bytes the paper's
+    radix needs with 11-bit digits (16 + 4 x 24 = 112 B/key, Eq. 4 with r = 11)."""
+    import collections
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    from gen import device as gdev
+    keys, vals = gdev.config3()
+    n = keys.numel()
+    out, vout = torch.empty_like(keys), torch.empty_like(vals)
+    call = lambda: ctx.sort(keys, vals=vals, out=out, vals_out=vout, force=ahs.AHS_RADIX,
+                            key_type=ahs.AHS_U64, stream=stream)
+    for _ in range(3):
+        r = call()
+    torch.cuda.synchronize()
+    ctx.trace(True)
+    times = timed_calls(call, reps, stream)
+    ctx.trace(False)
+    trace = ctx.trace_collect()
+    p50, p99 = percentiles(times)
+    kt = collections.defaultdict(lambda: [0, 0.0, 0])
+    for name, items, ms, _ in trace:
+        kt[name][0] += 1
+        kt[name][1] += ms
+        kt[name][2] += items
+    path_bytes = 112 * n
+    res = {"n": n, "strategy": ahs.STRATEGY_NAMES[r.strategy], "passes": int(r.info.passes),
+           "ms_p50": round(p50, 4), "ms_p99": round(p99, 4),
+           "gkeys_s_p50": round(n / (p50 / 1e3) / 1e9, 3),
+           "path_frac_112B": round(path_bytes / (p50 / 1e3) / 1e9 / peak, 4),
+           "kernels": kernel_table(kt, peak, 8, 4)}
+    del keys, vals, out, vout
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
@@ -451,9 +620,56 @@ def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
         res["per_array_ms"] = round(ms, 3)
         res["per_array_gkeys_s"] = round(total / (ms / 1e3) / 1e9, 3)
         res["batched_over_per_array"] = round(ms / statistics.median(times), 2)
+        # The served form on the same segments: every segment is one request,
+        # all submitted at once (the offered load exceeds capacity), sorted
+        # by the serving loop's continuous batching.
+        sv = run_served_segments(ctx.device, keys, out, offs_l, n_seg)
+        sv["served_over_per_array"] = round(sv["sustained_gkeys_s"] / res["per_array_gkeys_s"], 2)
+        res["served_same_segments"] = sv
     del keys, out
     torch.cuda.empty_cache()
     return res
+
+
+def run_served_segments(device: int, keys, out, offs_l, n_seg: int, budget: int = 64 << 30):
+    """Config 4's segments as served requests, all submitted at t = 0 from the
+    host: sustained Gkeys/s (wall time from the first submission to the last
+    completion) and latency percentiles."""
+    import ctypes
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    ctx = ahs.Context(device)
+    cfg = ahs.ahs_serve_config_t(budget, 1024, 100)
+    ahs.check(ahs.lib.ahs_serve_start(ctx.handle, ctypes.byref(cfg)), "ahs_serve_start")
+    base_in, base_out = keys.data_ptr(), out.data_ptr()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for s_ in range(n_seg):
+        b, e = offs_l[s_], offs_l[s_ + 1]
+        if e == b:
+            continue
+        req = ahs.ahs_request_t()
+        req.d_keys_in = base_in + 4 * b
+        req.d_keys_out = base_out + 4 * b
+        req.n = e - b
+        req.type = ahs.AHS_U32
+        tk = ctypes.c_uint64()
+        ahs.check(ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(req), ctypes.byref(tk)), "submit")
+        tickets.append(tk.value)
+    for tk in tickets:
+        r = ahs.ahs_result_t()
+        ahs.check(ahs.lib.ahs_serve_poll(ctx.handle, tk, 600000, ctypes.byref(r)), "poll")
+        ahs.check(r.status, "served request")
+    elapsed = time.perf_counter() - t0
+    st = ahs.ahs_serve_stats_t()
+    ahs.check(ahs.lib.ahs_serve_stats(ctx.handle, ctypes.byref(st)), "stats")
+    ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "stop")
+    ctx.close()
+    return {"requests": len(tickets), "seconds": round(elapsed, 3),
+            "sustained_gkeys_s": round(st.keys / elapsed / 1e9, 3),
+            "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
+            "batches": int(st.batches)}
 
 
 def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5,
@@ -613,10 +829,13 @@ def main():
                    help="diagnostic: one array of config 2 (a-f) or config 3, see --force")
     p.add_argument("--force", choices=["auto", "counting", "radix", "general"], default="auto")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
-    p.add_argument("--batch-segments", type=int, default=10_000,
+    p.add_argument("--batch-segments", type=int, default=100_000,
                    help="segments of the config-4 batch in the default run")
-    p.add_argument("--serve-load", type=float, default=5.0, help="offered Gkeys/s (default run)")
-    p.add_argument("--serve-seconds", type=float, default=4.0)
+    p.add_argument("--serve-loads", type=float, nargs="+", default=[2.0, 5.0, 10.0, 40.0],
+                   help="offered Gkeys/s of the served runs (the last one above capacity)")
+    p.add_argument("--serve-seconds", type=float, default=6.0)
+    p.add_argument("--cpu-segments", type=int, default=2000,
+                   help="config-4 segments the all-core oracle baseline sorts")
     p.add_argument("--batch", action="store_true", help="config 4 at full size: batched vs per-array")
     p.add_argument("--serve", action="store_true", help="config 5: offered loads 2/5/10 Gkeys/s")
     args = p.parse_args()
@@ -634,7 +853,7 @@ def main():
             out["batched"] = run_batched(ctx, 100_000, args.steps)
             ctx.close()
         if args.serve:
-            out["served"] = [run_served(local, load, args.serve_seconds) for load in (2.0, 5.0, 10.0)]
+            out["served"] = [run_served(local, load, args.serve_seconds) for load in args.serve_loads]
         print(json.dumps(out), flush=True)
         return
     if args.impl == "reference":

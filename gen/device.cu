@@ -85,6 +85,49 @@ __global__ void k_swaps_u32(uint32_t* a, unsigned long long n, unsigned long lon
     }
 }
 
+// Second workload family: Gaussian-shaped int32 keys by an integer
+// Irwin-Hall sum (12 uniform 32-bit integers from 6 draws per key), and
+// 60-bit k-mer keys of a synthetic repetitive genome (as gen/host.py).
+__global__ void k_gaussian_i32(int32_t* out, unsigned long long n, unsigned long long key,
+                               long long sigma_q16, unsigned long long start) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        long long S = 0;
+        for (int m = 0; m < 6; ++m) {
+            const unsigned long long r = draw(key, 6 * (start + i) + m);
+            S += (long long)(r >> 32) + (long long)(r & 0xffffffffull);
+        }
+        const long long d = S - 6ll * 4294967295ll;
+        out[i] = (int32_t)((d * sigma_q16) >> 48);
+    }
+}
+
+constexpr unsigned long long kKmerBlock = 1000, kKmerRepeats = 16, kKmerLen = 30;
+constexpr unsigned long long kKmerMut53 = 90071992547410ull;
+
+__device__ __forceinline__ unsigned long long kmer_base(unsigned long long p, unsigned long long key_rep,
+                                                        unsigned long long key_unit,
+                                                        unsigned long long key_mut) {
+    const unsigned long long r = __umul64hi(draw(key_rep, p / kKmerBlock), kKmerRepeats);
+    const unsigned long long u = draw(key_unit, r * kKmerBlock + p % kKmerBlock) >> 62;
+    const unsigned long long m = draw(key_mut, p);
+    return (m >> 11) < kKmerMut53 ? (m & 3ull) : u;
+}
+
+__global__ void k_kmer_u64(unsigned long long* out, unsigned long long n, unsigned long long key_rep,
+                           unsigned long long key_unit, unsigned long long key_mut,
+                           unsigned long long start) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride) {
+        unsigned long long k = 0;
+        for (unsigned long long j = 0; j < kKmerLen; ++j)
+            k |= kmer_base(start + i + j, key_rep, key_unit, key_mut) << (2 * (kKmerLen - 1 - j));
+        out[i] = k;
+    }
+}
+
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7FEB352Du;
@@ -200,6 +243,25 @@ int gen_swaps_u32(void* a, unsigned long long n, unsigned long long swaps, unsig
                   unsigned long long stream, void* st) {
     if (n == 0 || swaps == 0) return 0;
     k_swaps_u32<<<1, 1, 0, (cudaStream_t)st>>>((uint32_t*)a, n, swaps, stream_key(seed, stream));
+    return (int)cudaGetLastError();
+}
+
+int gen_gaussian_i32(void* out, unsigned long long n, unsigned long long seed,
+                     unsigned long long stream, long long sigma_q16, unsigned long long start,
+                     void* st) {
+    if (n == 0) return 0;
+    k_gaussian_i32<<<grid(n), 256, 0, (cudaStream_t)st>>>((int32_t*)out, n, stream_key(seed, stream),
+                                                          sigma_q16, start);
+    return (int)cudaGetLastError();
+}
+
+int gen_kmer_u64(void* out, unsigned long long n, unsigned long long seed, unsigned long long stream,
+                 unsigned long long start, void* st) {
+    if (n == 0) return 0;
+    k_kmer_u64<<<grid(n), 256, 0, (cudaStream_t)st>>>((unsigned long long*)out, n,
+                                                      stream_key(seed, stream),
+                                                      stream_key(seed, stream + 1),
+                                                      stream_key(seed, stream + 2), start);
     return (int)cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ def lib():
         L.gen_ramp_replace.argtypes = [vp, u64, u64, u64, u64, u64, vp]
         L.gen_swaps_u32.argtypes = [vp, u64, u64, u64, u64, vp]
         L.gen_batch_u32.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp, ctypes.c_uint, vp]
+        L.gen_gaussian_i32.argtypes = [vp, u64, u64, u64, ctypes.c_longlong, u64, vp]
+        L.gen_kmer_u64.argtypes = [vp, u64, u64, u64, u64, vp]
         L.gen_batch_swaps.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp]
         _lib = L
     return _lib
@@ -59,6 +61,22 @@ def zipf_u32(n, seed, stream_values, stream_ranks, n_values=1024, s=1.1, start=0
     _ok(lib().gen_zipf_u32(out.data_ptr(), n, seed, stream_ranks, cdf.data_ptr(), vals.data_ptr(),
                            n_values, start, _st()))
     torch.cuda.synchronize()
+    return out
+
+
+def gaussian_i32(n, seed, stream, k, start=0):
+    """int32 keys shaped like N(0, k/4) (as gen.host.gaussian_i32)."""
+    import torch
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    _ok(lib().gen_gaussian_i32(out.data_ptr(), n, seed, stream, H.gauss_sigma_q16(k), start, _st()))
+    return out
+
+
+def kmer_u64(n, seed, stream, start=0):
+    """uint64 60-bit k-mer keys (int64 tensor; as gen.host.kmer_u64)."""
+    import torch
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _ok(lib().gen_kmer_u64(out.data_ptr(), n, seed, stream, start, _st()))
     return out
 
 

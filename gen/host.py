@@ -198,6 +198,70 @@ def ramp_u64(n: int, seed: int, t0: int = 1_700_000_000_000_000_000,
 
 
 # ----------------------------------------------------------------------------
+# Second workload family (Section III-B, Table VII)
+# ----------------------------------------------------------------------------
+
+GAUSS_TERMS = 12          # Irwin-Hall: a sum of 12 uniform 32-bit integers
+KMER_LEN = 30             # k-mers of 30 bases, 2 bits each: 60-bit keys, k = 4^30
+KMER_BLOCK = 1000         # bases per block of the synthetic genome
+KMER_REPEATS = 16         # distinct repeat units the blocks are copied from
+KMER_MUT_53 = 90071992547410   # P(point mutation) = 0.01 on the 53-bit integer scale
+
+
+def gauss_sigma_q16(k: int) -> int:
+    """sigma = sqrt(k / 4) = sqrt(k) / 2 in 16.16 fixed point (the one fp64
+    step, taken on the host and passed to both generators)."""
+    return int(round(math.sqrt(k) / 2.0 * 65536.0))
+
+
+def gaussian_i32(n: int, seed: int, stream: int, k: int, start: int = 0) -> np.ndarray:
+    """n int32 keys shaped like N(0, sigma^2 = k/4) (Section III-B).  Integer
+    only, so host and device agree bit for bit: S is the sum of 12 uniform
+    32-bit integers (the top and bottom halves of 6 draws per key), whose
+    mean 6 (2^32 - 1) and standard deviation ~2^32 make
+    Z = (S - mean) / 2^32 close to a standard normal (Irwin-Hall);
+    key = floor((S - 6 (2^32 - 1)) * sigma_q16 / 2^48)."""
+    sq = gauss_sigma_q16(k)
+    d = draws(seed, stream, 6 * start, 6 * n).reshape(n, 6) if n else np.zeros((0, 6), U64)
+    hi = (d >> U64(32)).astype(np.int64)
+    lo = (d & U64(0xFFFFFFFF)).astype(np.int64)
+    S = hi.sum(axis=1) + lo.sum(axis=1)
+    dev_ = S - 6 * (2**32 - 1)
+    return ((dev_ * sq) >> 48).astype(np.int32)
+
+
+def kmer_bases(count: int, seed: int, stream: int, start: int = 0) -> np.ndarray:
+    """Bases (0..3) of a synthetic repetitive genome at positions
+    [start, start + count): position p lies in block p // 1000, a copy of one
+    of 16 repeat units (chosen per block), at offset p % 1000 of it; each
+    position mutates to a random base with probability 0.01."""
+    if count == 0:
+        return np.zeros(0, dtype=np.uint64)
+    p = np.arange(start, start + count, dtype=np.int64)
+    blocks = p // KMER_BLOCK
+    b0 = int(blocks[0])
+    nb = int(blocks[-1]) - b0 + 1
+    with np.errstate(over="ignore"):
+        rep = (below64(draws(seed, stream, b0, nb), KMER_REPEATS)).astype(np.int64)
+    unit = draws(seed, stream + 1, 0, KMER_REPEATS * KMER_BLOCK) >> U64(62)
+    base = unit[rep[blocks - b0] * KMER_BLOCK + (p % KMER_BLOCK)]
+    m = draws(seed, stream + 2, start, count)
+    mut = (m >> U64(11)) < U64(KMER_MUT_53)
+    base = np.where(mut, m & U64(3), base)
+    return base.astype(U64)
+
+
+def kmer_u64(n: int, seed: int, stream: int, start: int = 0) -> np.ndarray:
+    """n uint64 k-mer keys: key i packs the 30 bases at positions
+    i .. i + 29 of the genome, first base in the high bits (60-bit keys)."""
+    b = kmer_bases(n + KMER_LEN - 1, seed, stream, start)
+    key = np.zeros(n, dtype=U64)
+    for j in range(KMER_LEN):
+        key |= b[j:j + n] << U64(2 * (KMER_LEN - 1 - j))
+    return key
+
+
+# ----------------------------------------------------------------------------
 # The workload configurations
 # ----------------------------------------------------------------------------
 

@@ -120,6 +120,7 @@ typedef struct {
     uint64_t workspace_limit;    /* bytes of device workspace the ctx may hold, 0 = no limit */
     int32_t timing;              /* 1: record per-phase device times into info structs */
     uint32_t debug_flags;        /* AHS_DEBUG_* test hooks, 0 in normal use */
+    const char* tuning_path;     /* tuned-shape table (ahs_load_tuning); NULL: compiled defaults */
 } ahs_config_t;
 
 /* Test hook: in every radix pass, tile 1 does not publish its counts, so the
@@ -168,6 +169,22 @@ void ahs_destroy(ahs_ctx* ctx);
 const char* ahs_status_str(ahs_status s);
 /* Text of the last CUDA error seen by this ctx ("" if none). */
 const char* ahs_last_cuda_error(const ahs_ctx* ctx);
+/* Load (or replace) the tuned-shape table of the context from a text file
+ * written by the library's autotuner (NULL: back to the compiled defaults).
+ * The table sets the largest digit width of the stable LSD radix passes
+ * (Eq. 4: d = ceil(bitlen(k - 1) / r) passes of r <= 11 bits, chosen per key
+ * width, payload and range by measured time) and the batched form's
+ * one-block cutoff.  Format:
+ *   ahs-tuning 1
+ *   radix_bits <key bytes 4|8> <payload 0|1> <span bits 1..64> <digit bits 1..11>
+ *   batch_small_cutoff <keys 0..8192>
+ * AHS_ERR_NOT_FOUND if the file is missing or malformed (the table is then
+ * unchanged). */
+ahs_status ahs_load_tuning(ahs_ctx* ctx, const char* path);
+/* The radix plan the context's table gives for a key range: pass count and
+ * the digit width of the first pass (host only, pure). */
+ahs_status ahs_tuned_radix_bits(const ahs_ctx* ctx, uint32_t key_bytes, int32_t has_payload,
+                                uint64_t span, uint32_t* passes, uint32_t* digit_bits);
 /* Load (or replace) the MODEL profile's tree table from a text file. */
 ahs_status ahs_load_model(ahs_ctx* ctx, const char* path);
 

@@ -70,6 +70,36 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_STD_SRC = os.path.join(_HERE, "stdsort.cpp")
+_STD_LIB = os.path.join(_HERE, "libahs_stdsort.so")
+
+
+def build_std(force: bool = False) -> str:
+    """Compile the std::sort context routine (g++, -O2)."""
+    if force or not os.path.exists(_STD_LIB) or os.path.getmtime(_STD_LIB) < os.path.getmtime(_STD_SRC):
+        tmp = _STD_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _STD_SRC])
+        os.replace(tmp, _STD_LIB)
+    return _STD_LIB
+
+
+_std = None
+
+
+def std_sort(keys: np.ndarray, stable: bool = False) -> np.ndarray:
+    """libstdc++ std::sort (or std::stable_sort) of uint32 keys: context for the
+    CPU baseline, not part of the oracle."""
+    global _std
+    if _std is None:
+        _std = ctypes.CDLL(build_std())
+        _std.orc_std_sort_u32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                          ctypes.c_int]
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    out = np.empty_like(keys)
+    _check(_std.orc_std_sort_u32(_ptr(keys), _ptr(out), len(keys), int(stable)), "std_sort")
+    return out
+
+
 _lib = None
 
 

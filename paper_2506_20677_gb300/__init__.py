@@ -47,7 +47,7 @@ class ahs_config_t(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("select_mode", ctypes.c_int),
                 ("thresholds", ahs_thresholds_t), ("model_path", ctypes.c_char_p),
                 ("workspace_limit", ctypes.c_uint64), ("timing", ctypes.c_int32),
-                ("debug_flags", ctypes.c_uint32)]
+                ("debug_flags", ctypes.c_uint32), ("tuning_path", ctypes.c_char_p)]
 
 
 class ahs_sort_info_t(ctypes.Structure):
@@ -103,6 +103,8 @@ SIGNATURES = {
     "ahs_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ahs_last_cuda_error": (ctypes.c_char_p, [_ctx]),
     "ahs_load_model": (ctypes.c_int, [_ctx, ctypes.c_char_p]),
+    "ahs_load_tuning": (ctypes.c_int, [_ctx, ctypes.c_char_p]),
+    "ahs_tuned_radix_bits": (ctypes.c_int, [_ctx, _u32, _i32, _u64, _P(_u32), _P(_u32)]),
     "ahs_trace_enable": (ctypes.c_int, [_ctx, _i32]),
     "ahs_trace_collect": (ctypes.c_int, [_ctx, _P(ahs_trace_entry_t), _u32, _P(_u32)]),
     "ahs_features": (ctypes.c_int, [_ctx, _vp, _u64, ctypes.c_int, _vp, _P(ahs_features_t)]),
@@ -188,6 +190,9 @@ class SortResult:
 # Tree table trained on GB300 timing labels (selector/labels_gb300.json);
 # the default for AHS_SEL_MODEL contexts.
 SHIPPED_TREES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector", "ahs_trees.txt")
+# Kernel shapes tuned on GB300 (autotune.py); every context loads it when present.
+SHIPPED_TUNING = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector",
+                              "tuning_gb300.txt")
 
 
 class Context:
@@ -195,7 +200,7 @@ class Context:
 
     def __init__(self, device: int = 0, select_mode: int = AHS_SEL_GB300, model_path=None,
                  timing: bool = False, workspace_limit: int = 0, thresholds=None,
-                 debug_flags: int = 0):
+                 debug_flags: int = 0, tuning_path="shipped"):
         cfg = ahs_config_t()
         lib.ahs_default_config(ctypes.byref(cfg))
         cfg.device = device
@@ -207,6 +212,10 @@ class Context:
             model_path = SHIPPED_TREES
         self._model_path = None if model_path is None else os.fsencode(model_path)
         cfg.model_path = self._model_path
+        if tuning_path == "shipped":
+            tuning_path = SHIPPED_TUNING if os.path.exists(SHIPPED_TUNING) else None
+        self._tuning_path = None if tuning_path is None else os.fsencode(tuning_path)
+        cfg.tuning_path = self._tuning_path
         if thresholds is not None:
             cfg.thresholds = thresholds
         self.handle = ctypes.c_void_p()
@@ -258,6 +267,18 @@ class Context:
         check(lib.ahs_features(self.handle, ctypes.c_void_p(keys.data_ptr()), keys.numel(), kt,
                                _stream_handle(stream), ctypes.byref(f)), "ahs_features", self.handle)
         return f
+
+    def load_tuning(self, path):
+        """Replace the tuned-shape table (None: compiled defaults)."""
+        check(lib.ahs_load_tuning(self.handle, None if path is None else os.fsencode(path)),
+              "ahs_load_tuning", self.handle)
+
+    def radix_plan(self, span: int, key_bytes: int = 4, has_payload: bool = False):
+        """(passes, digit bits of the first pass) of the stable LSD radix for a key range."""
+        p, b = ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib.ahs_tuned_radix_bits(self.handle, key_bytes, int(has_payload), span,
+                                       ctypes.byref(p), ctypes.byref(b)), "ahs_tuned_radix_bits")
+        return p.value, b.value
 
     def select(self, f: ahs_features_t, mode: int, key_bytes: int = 4, has_payload: bool = False):
         out = ctypes.c_int()

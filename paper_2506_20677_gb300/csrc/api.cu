@@ -91,11 +91,22 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
     s.host_rec = ctx->h_rec;
     s.host_hist = ctx->h_hist;
     s.skip_sorted = skip_sorted;
+    const size_t mark = ctx->tracer.records.size();
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
+    // The histogram kernel returned at once for an input found in order: its
+    // trace entry processed no keys.
+    if (skip_sorted && ctx->h_rec->descents == 0)
+        for (size_t i = mark; i < ctx->tracer.records.size(); ++i)
+            if (std::strcmp(ctx->tracer.records[i].name, "features_histogram") == 0)
+                ctx->tracer.records[i].items = 0;
     to_public(*ctx->h_rec, kd, out);
     return AHS_OK;
+}
+
+uint32_t radix_digit_bits(const ahs_ctx* ctx, uint32_t key_bytes, bool payload, uint64_t span) {
+    return ctx->tuning.radix_digit_bits(key_bytes, payload, bitlen64(span));
 }
 
 // Whether AUTO selection under the context's profile returns an input already
@@ -246,18 +257,18 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
             return run_msd_radix(ctx, kin, kout, n, kd, min_ord, hist, f.hist_shift, group_slots(f),
                                  static_cast<char*>(ctx->ws) + freg, st, passes, buckets);
         }
-        const RadixPlan plan = radix_plan(f.span);
+        const RadixPlan plan = radix_plan(f.span, radix_digit_bits(ctx, kd.bytes, vin != nullptr, f.span));
         if (plan.passes == 0) {
             e = launch_copy32(kout, kin, n * kd.bytes / 4, ctx->sms, st);
             if (e == cudaSuccess && vin) e = launch_copy32(vout, vin, n, ctx->sms, st);
             return cuda_status(ctx, e);
         }
         if (n >= (1ull << 30)) return AHS_ERR_UNIMPLEMENTED;
-        const size_t need = radix_scratch_bytes(n, kd.bytes, vin != nullptr, plan.passes);
+        const size_t need = radix_scratch_bytes(n, kd.bytes, vin != nullptr, plan);
         ahs_status rc = ensure_workspace(ctx, freg + need);
         if (rc != AHS_OK) return rc;
         RadixScratch rs = radix_carve(static_cast<char*>(ctx->ws) + freg, n, kd.bytes,
-                                      vin != nullptr, plan.passes);
+                                      vin != nullptr, plan);
         e = launch_radix_sort(kin, kout, vin, vout, n, kd, min_ord, plan, rs, ctx->d_rec,
                               ctx->d_err, ctx->sms, st,
                               (ctx->cfg.debug_flags & AHS_DEBUG_STALL_ONE_TILE) ? 1u : ~0u);
@@ -333,6 +344,13 @@ ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg) {
     }
     ctx->custom = ctx->cfg.thresholds;
     ctx->device = ctx->cfg.device;
+    if (ctx->cfg.tuning_path) {
+        std::string why;
+        if (!ctx->tuning.load(ctx->cfg.tuning_path, &why)) {
+            delete ctx;
+            return AHS_ERR_NOT_FOUND;
+        }
+    }
     if (ctx->device < 0) {
         // Host-only context: selection and model loading, no device work.
         if (ctx->cfg.model_path) {
@@ -399,6 +417,7 @@ void ahs_destroy(ahs_ctx* ctx) {
     for (auto& e : ctx->tracer.pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->aux) cudaFree(ctx->aux);
+    if (ctx->side) cudaFree(ctx->side);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->d_rec) cudaFree(ctx->d_rec);
     if (ctx->h_rec) cudaFreeHost(ctx->h_rec);
@@ -438,6 +457,26 @@ ahs_status ahs_trace_collect(ahs_ctx* ctx, ahs_trace_entry_t* out, uint32_t cap,
 
 const char* ahs_last_cuda_error(const ahs_ctx* ctx) {
     return ctx ? ctx->last_cuda_error.c_str() : "";
+}
+
+ahs_status ahs_load_tuning(ahs_ctx* ctx, const char* path) {
+    if (!ctx) return AHS_ERR_INVALID_ARG;
+    if (!path) {
+        ctx->tuning.clear();
+        return AHS_OK;
+    }
+    std::string why;
+    return ctx->tuning.load(path, &why) ? AHS_OK : AHS_ERR_NOT_FOUND;
+}
+
+ahs_status ahs_tuned_radix_bits(const ahs_ctx* ctx, uint32_t key_bytes, int32_t has_payload,
+                                uint64_t span, uint32_t* passes, uint32_t* digit_bits) {
+    if (!ctx || !passes || !digit_bits || (key_bytes != 4 && key_bytes != 8))
+        return AHS_ERR_INVALID_ARG;
+    const RadixPlan p = radix_plan(span, radix_digit_bits(ctx, key_bytes, has_payload != 0, span));
+    *passes = p.passes;
+    *digit_bits = p.passes ? p.bits[0] : 0;
+    return AHS_OK;
 }
 
 ahs_status ahs_load_model(ahs_ctx* ctx, const char* path) {

@@ -426,6 +426,10 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
         // Counting here is keys-only with the whole range in one CTA's
         // shared memory; wider ranges and payloads take the radix class.
         if (st_s == AHS_COUNTING && (payload || f.span >= kCountMaxBins)) st_s = AHS_RADIX;
+        // The tuned cutoff: segments this small are sorted by one CTA
+        // whatever their strategy (the launch is cheaper than a class pass).
+        const uint32_t cut = ctx->tuning.batch_small_cutoff();
+        if (cut && n > 1 && n <= cut && n <= kBucketCap && st_s != AHS_IDENTITY) st_s = AHS_SMALL;
         const SegRange r{b, (uint32_t)n, f.min_bits ^ kd.flip};
         switch (st_s) {
         case AHS_IDENTITY: ident.push_back(r); break;

@@ -12,6 +12,7 @@
 #include "internal.h"
 #include "select.h"
 #include "trace.h"
+#include "tuning.h"
 
 namespace ahs {
 struct ServeState;   // serve.cpp
@@ -39,10 +40,14 @@ struct ahs_ctx {
     size_t aux_bytes = 0;
     void* h_stage = nullptr;
     size_t h_stage_bytes = 0;
+    // Growable side buffer of the exact-entropy mode (its sorted copy).
+    void* side = nullptr;
+    size_t side_bytes = 0;
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string last_cuda_error;
     ahs::TreeModel model;
+    ahs::Tuning tuning;
     ahs::Tracer tracer;
 
     ahs::ServeState* serve = nullptr;   // owned; released by ahs_serve_stop
@@ -61,6 +66,8 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
                         cudaStream_t st, ahs_features_t* out, bool skip_sorted = false);
 void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out);
 ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload);
+// Whether AUTO under the context's profile returns an input in order as it is.
+bool sorted_identity(const ahs_ctx* ctx);
 // Run one strategy on device-resident inputs whose features are in ctx->d_rec
 // and whose feature scratch (histogram) is at the start of ctx->ws.
 ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kout,
@@ -68,6 +75,8 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
                         const ahs_features_t& f, cudaStream_t st, uint32_t* passes,
                         uint32_t* buckets);
 size_t features_region(int sms);
+// Largest digit width of the stable LSD passes for this key range (tuned).
+uint32_t radix_digit_bits(const ahs_ctx* ctx, uint32_t key_bytes, bool payload, uint64_t span);
 ahs_status check_device_error(ahs_ctx* ctx, cudaStream_t st);
 // Grow the auxiliary device buffer / pinned host staging (may synchronise).
 ahs_status ensure_aux(ahs_ctx* ctx, size_t bytes);
@@ -94,10 +103,13 @@ ahs_status run_samplesort(ahs_ctx* ctx, const void* kin, void* kout, const uint3
                           const HistView* hist = nullptr,
                           uint64_t min_ord = 0, uint32_t shift = 0, uint32_t group = 0);
 
-// Keys-only radix sort, most significant digit first: two partition passes by
-// the high and low byte of the feature histogram's bin (exact bucket sizes
-// from `hist`, the host copy of the histogram, bin = (ord(x) - min_ord) >> shift),
-// then per-bin shared-memory sorts.  scratch: samplesort_scratch_bytes().
+// Keys-only radix sort, most significant digit first: partition passes by the
+// feature histogram's bin -- level 1 by the bin's high byte, or by runs of
+// consecutive bins of about n / 256 keys when the blocks of 256 bins are
+// unbalanced (a heavy bin is then a bucket after one pass), level 2 by the
+// single bin -- with exact bucket sizes from `hist` (the host copy of the
+// histogram, bin = (ord(x) - min_ord) >> shift), then per-bin shared-memory
+// sorts.  scratch: samplesort_scratch_bytes().
 ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
                          uint64_t min_ord, const HistView& hist,
                          uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,

@@ -83,22 +83,26 @@ cudaError_t launch_zero32(void* dst, uint64_t words, int sms, cudaStream_t st);
 cudaError_t launch_transfer(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 // --------------------------------------------------------------------- radix
+constexpr uint32_t kMaxRadixPasses = 8;
 struct RadixPlan {
     uint32_t passes;
-    uint32_t shift[8];   // low bit of each pass's digit
-    uint32_t bits[8];    // digit width of each pass (<= 8)
+    uint32_t radix;                       // digit alphabet of every pass: 16, 256, 512, 1024 or 2048
+    uint32_t shift[kMaxRadixPasses];      // low bit of each pass's digit
+    uint32_t bits[kMaxRadixPasses];       // digit width of each pass (<= log2 radix)
 };
-RadixPlan radix_plan(uint64_t span);
-size_t radix_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes);
+// Passes and digit widths for digits of at most max_bits bits (1..11).
+RadixPlan radix_plan(uint64_t span, uint32_t max_bits = 8);
+size_t radix_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals, const RadixPlan& plan);
 struct RadixScratch {
     void* keys_tmp;                   // n keys
     uint32_t* vals_tmp;               // n payload words (or null)
-    unsigned long long* digit_hist;   // 8 x 256 (u64)
-    uint32_t* status;                 // passes x tiles x 256 look-back words
-    uint32_t* tile_counters;          // 8
+    unsigned long long* digit_hist;   // kMaxRadixPasses x 2048 (u64), then the digit bases (u32)
+    uint32_t* status;                 // passes x tiles x radix look-back words
+    uint32_t* tile_counters;          // kMaxRadixPasses
     uint64_t tiles;
 };
-RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_vals, uint32_t passes);
+RadixScratch radix_carve(void* base, uint64_t n, uint32_t key_bytes, bool has_vals,
+                         const RadixPlan& plan);
 // Stable LSD radix sort over ord(x) - min (onesweep passes with decoupled look-back).
 // stall_tile: a tile that withholds its look-back publication (test hook), or ~0u.
 cudaError_t launch_radix_sort(const void* keys_in, void* keys_out, const uint32_t* vals_in,

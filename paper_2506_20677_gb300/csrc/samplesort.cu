@@ -415,7 +415,7 @@ struct FastSmem {
     uint16_t bid[TILE];
     uint32_t hist[kCols];
     uint32_t tile_start[kCols];
-    uint32_t gbase[kCols];
+    K* gptr[kCols];           // where the tile's run of each bucket goes, less its staged start
     uint32_t scan[kFastThreads / 32 + 1];
     SegDesc seg[kSegCache];   // the pass's segments, when it has no tile list
     TileDesc tile[2];         // the tile in buf[s]
@@ -438,13 +438,18 @@ __device__ __forceinline__ TileDesc tile_of(const SegDesc* segs, uint32_t nsegs,
     return {segs[lo].begin + off, size - off < tile_keys ? size - off : tile_keys, lo};
 }
 
+// dsel (nullable): one byte per (segment, bucket) cursor; a bucket whose byte
+// is set is written to dst2 instead of dst (at the same offsets), so that
+// buckets final after this pass can land in the output while the others go
+// to the temporary buffer of the next pass.
 template <typename K, int MODE, bool GROUP = false>
 __global__ void __launch_bounds__(kFastThreads, 2)
 ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* __restrict__ tiles,
                 const SegDesc* __restrict__ segs, uint32_t nsegs, uint32_t ntiles,
                 const K* __restrict__ splitters,
                 const uint32_t* __restrict__ nsplit, K flip, uint32_t shift,
-                uint32_t* __restrict__ cursor, uint32_t* __restrict__ err) {
+                uint32_t* __restrict__ cursor, uint32_t* __restrict__ err,
+                K* __restrict__ dst2 = nullptr, const uint8_t* __restrict__ dsel = nullptr) {
     constexpr int IPT = FastCfg<K>::kIpt;
     constexpr uint32_t TILE = FastCfg<K>::kTileKeys;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -538,16 +543,22 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         __syncthreads();
 
         // Reserve each bucket's run in the segment; tile-local run starts.
+        // A run that would leave its segment (a histogram that does not
+        // describe these keys) is reported and not written.
         {
             const uint32_t j = tid;   // kFastThreads == kCols
             const uint32_t c = S.hist[j];
             S.hist[j] = 0;
             // c == 0 for every column past the classifier's buckets.
-            const uint32_t base = c ? atomicAdd(&cursor[(size_t)t.seg * cursor_stride<MODE>() + j], c) : 0u;
+            const size_t cj = (size_t)t.seg * cursor_stride<MODE>() + j;
+            const uint32_t base = c ? atomicAdd(&cursor[cj], c) : 0u;
             uint32_t total;
             const uint32_t ex = block_exclusive_scan<kFastThreads>(c, S.scan, &total);
             S.tile_start[j] = ex;
-            S.gbase[j] = base - ex;
+            K* d = (dsel != nullptr && c && dsel[cj]) ? dst2 : dst;
+            const bool inside = (unsigned long long)base + c <= sg.size;
+            if (!inside) report_error(err, kDevBadState);
+            S.gptr[j] = inside ? d + sg.begin + ((long long)base - (long long)ex) : nullptr;
         }
         __syncthreads();
 
@@ -566,16 +577,14 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         }
         __syncthreads();
 
-        K* out = dst + sg.begin;
 #pragma unroll 4
         for (uint32_t j = tid; j < t.size; j += kFastThreads) {
             const K x = buf[j];
             uint32_t b;
             if constexpr (MODE == kDigit) b = cls((K)(x ^ flip));
             else b = S.bid[j];
-            const uint32_t gp = S.gbase[b] + j;
-            if (gp >= sg.size) { report_error(err, kDevBadState); continue; }
-            out[gp] = x;
+            K* const o = S.gptr[b];
+            if (o != nullptr) o[j] = x;
         }
         __syncthreads();
         if (tid == 0) {
@@ -959,14 +968,15 @@ ahs_status radix_segs_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin
 // u = ord(x) - min (bin = u >> s, s = bitlen(span) - 16), so partition passes
 // whose bucket boundaries are bin boundaries know their bucket sizes without a
 // counting pass:
-//   RADIX (most significant digit first): pass 1 by the high byte of the bin,
-//     pass 2 by its low byte -- every bin's keys then sit at their final
-//     position, and a bin holds keys that differ only in their low s bits.
-//   GENERAL (sample sort with splitters from the histogram): level 1 splits at
-//     boundaries of 256-bin blocks when no block holds more than twice its
-//     share of the keys (classified by bit extraction), else at runs of bins
-//     of about n / 256 keys each (classified by splitter search); level 2 cuts
-//     each run into buckets spanning at most 16 bits of u.
+//   Both strategies partition most significant digit first, by the bin:
+//   level 1 splits at boundaries of 256-bin blocks (the bin's high byte, by
+//   bit extraction) when no block holds more than twice its share of the
+//   keys, else at runs of consecutive bins of about n / 256 keys each (a
+//   digit of variable width, found by splitter search), so that a bin heavier
+//   than its share is a bucket of its own after one pass -- the common case
+//   of the low-entropy inputs the radix strategy is chosen for; level 2 cuts
+//   each run into buckets spanning at most 16 bits of u (one bin when the
+//   bins are 2^16 wide).  RADIX and GENERAL differ only in their trace names.
 // Buckets that fit a CTA are sorted in shared memory; larger ones (bins heavier
 // than a CTA, with no finer information in the histogram) are checked for a
 // single value and otherwise sample-sorted.  All lists of a sort are built on
@@ -1123,7 +1133,8 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     // final buckets), sized by upper bounds so that no upload has to wait for
     // an earlier one: the host prepares level 2 while level 1 runs, and the
     // bucket lists while level 2 runs.
-    const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(2 * kSlots * sizeof(K));
+    const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(2 * kSlots * sizeof(K)) +
+                        a256(kCols);
     const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(256 * kCols * 4) +
                              a256(256 * 2 * kSlots * sizeof(K)));
     const size_t class_cap = nbins + n / kCopyChunk + 8;   // entries of one class region
@@ -1145,10 +1156,12 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         uint32_t dshift = 0;
         const K* src = nullptr;
         K* dst = nullptr;
+        K* dst2 = nullptr;              // buckets whose dsel byte is set go here
+        std::vector<uint8_t> dsel;      // per (segment, bucket) cursor; empty: all to dst
     };
     // Lists of `P` into the blob, then its launch (after the blob's copy).
     struct Placed {
-        size_t o_segs, o_cur, o_spl;
+        size_t o_segs, o_cur, o_spl, o_dsel;
         uint32_t ns, nt;
         uint64_t keys;
     };
@@ -1187,6 +1200,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         pl.o_segs = blob.add(segs.data(), segs.size() * sizeof(SegDesc));
         pl.o_cur = blob.add(cur.data(), cur.size() * 4);
         pl.o_spl = P.digit ? 0 : blob.add(spl.data(), spl.size() * sizeof(K));
+        pl.o_dsel = P.dsel.empty() ? 0 : blob.add(P.dsel.data(), P.dsel.size());
         pl.ns = (uint32_t)segs.size();
         pl.nt = nt;
         return pl;
@@ -1202,27 +1216,36 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         uint32_t* d_cur = reinterpret_cast<uint32_t*>(aux + window + pl.o_cur);
         TraceScope ts(msd ? "msd_scatter" : "sample_scatter", pl.keys, st);
         const K* spl = reinterpret_cast<const K*>(w + pl.o_spl);
+        const uint8_t* dsel = P.dsel.empty() ? nullptr : reinterpret_cast<const uint8_t*>(w + pl.o_dsel);
         if (P.digit && P.group)
             ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
                 P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
-                ctx->d_err);
+                ctx->d_err, P.dst2, dsel);
         else if (P.digit)
             ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
                 P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
-                ctx->d_err);
+                ctx->d_err, P.dst2, dsel);
         else if (P.group)
             ss_scatter_keys<K, kRange, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err);
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err,
+                P.dst2, dsel);
         else
             ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err);
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err,
+                P.dst2, dsel);
         return cudaGetLastError();
     };
 
-    // Level 1: input -> temporary.
+    // A level-1 run of bins [b0, b1) is split by level 2 when it holds more
+    // than a CTA's keys in more than one bin.
+    auto splits_further = [&](uint32_t b0, uint32_t b1) {
+        return binpos[b1] - binpos[b0] > kBucketCap && b1 - b0 > 1;
+    };
+
+    // Level 1: input -> temporary (runs that level 2 splits) or output.
     const unsigned long long share = std::max<unsigned long long>((n + 255) / 256, 1);
     bool blocks = nbins > 256;
-    for (uint32_t c = 0; !msd && blocks && c * 256 < nbins; ++c)
+    for (uint32_t c = 0; blocks && c * 256 < nbins; ++c)
         blocks = binpos[std::min(nbins, (c + 1) * 256)] - binpos[c * 256] <= 2 * share;
     std::vector<uint32_t> s1;
     if (blocks) {
@@ -1246,6 +1269,14 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         P1.group = (group & kGroupLevel1) != 0 || d1 >= kGroupCollide;
         P1.src = kin;
         P1.dst = ktmp;
+        // Runs that no later pass splits (at most a CTA's keys, or one bin)
+        // are written straight to the output.
+        P1.dst2 = kout;
+        P1.dsel.assign(cursor_stride<kDigit>(), 0);
+        for (size_t g = 0; g <= s1.size(); ++g) {
+            const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
+            P1.dsel[g] = !splits_further(b0, b1);
+        }
         Blob A{stage, capA};
         const Placed pl = place(P1, A);
         if (A.overflow()) return AHS_ERR_CUDA;
@@ -1279,13 +1310,13 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     Pd.dshift = shift;
     Pd.src = Pr.src = ktmp;
     Pd.dst = Pr.dst = kout;
-    const uint32_t span_bins = msd || shift >= 16 ? 1u : 1u << (16 - shift);
+    const uint32_t span_bins = shift >= 16 ? 1u : 1u << (16 - shift);
     // Per level-1 run: -1 if it is final, else (pass, index) of its level-2 segment.
     std::vector<int32_t> split2(s1.size() + 1, -1);
     for (size_t g = 0; g <= s1.size(); ++g) {
         const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
         const unsigned long long sz = binpos[b1] - binpos[b0];
-        if (sz <= kBucketCap || b1 - b0 == 1) continue;
+        if (!splits_further(b0, b1)) continue;
         std::vector<uint32_t> st2 = group_bins(hist, b0, b1, kBucketCap / 2,
                                                std::max<uint32_t>(span_bins, (b1 - b0 + 255) / 256));
         bool single = (b1 - b0 <= 256) && st2.size() == b1 - b0 - 1;
@@ -1310,8 +1341,8 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         }
     }
     // Final buckets, into the class regions of the third window: level-1 runs
-    // that are final (from the temporary buffer) and the sub-buckets of the
-    // level-2 segments (from the output).
+    // that are final and the sub-buckets of the level-2 segments, all in the
+    // output by now and sorted there in place.
     ClassLists cl;
     cl.cap = class_cap;
     for (int k = 0; k < kBucketClasses; ++k)
@@ -1321,10 +1352,9 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         const unsigned long long sz = binpos[b1] - binpos[b0];
         if (sz == 0) continue;
         if (split2[g] < 0) {
+            // Already in the output (level 1 wrote it there): sorted in place.
             if (sz <= kBucketCap && sz > 1)
-                cl.add(final_bucket_bounded(binpos[b0], (uint32_t)sz, 0, bin_lo(b0), range_bits(b0, b1)));
-            else
-                cl.add(final_bucket(binpos[b0], (uint32_t)sz, 0, false));   // copy out
+                cl.add(final_bucket_bounded(binpos[b0], (uint32_t)sz, 1, bin_lo(b0), range_bits(b0, b1)));
             if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
             continue;
         }

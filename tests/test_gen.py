@@ -4,6 +4,7 @@ import math
 import numpy as np
 
 from gen import host as g
+from gen import host as H
 
 
 def test_splitmix64_published_sequence():
@@ -85,3 +86,28 @@ def test_config4_layout():
     assert np.all(np.bincount(T) > 24000)
     s = g.config4_segment(5, int(L[5]), int(T[5]))
     assert len(s) == L[5]
+
+
+def test_gaussian_shape_and_determinism():
+    """Irwin-Hall sum of 12 uniforms: mean ~0 and sd ~sqrt(k/4); a prefix and
+    an offset start give the same keys as one call (counter-based)."""
+    for k in (10**2, 10**4, 10**6):
+        g = H.gaussian_i32(400_000, 1, 30, k)
+        sd = (k / 4) ** 0.5
+        assert abs(g.std() - sd) < 0.01 * sd + 0.5
+        assert abs(g.mean()) < 0.02 * sd + 1.0
+        # Irwin-Hall with 12 terms is bounded at 6 sd
+        assert g.min() >= -6 * sd - 1 and g.max() <= 6 * sd
+    a = H.gaussian_i32(1000, 1, 30, 10**4)
+    assert np.array_equal(a[300:], H.gaussian_i32(700, 1, 30, 10**4, start=300))
+
+
+def test_kmer_shape():
+    """60-bit keys, each the next window of the same base sequence."""
+    k = H.kmer_u64(50_000, 2, 60)
+    assert int(k.max()).bit_length() <= 60
+    # consecutive windows overlap in 29 bases: key[i+1] >> 2 == key[i] & (2^58 - 1)
+    assert np.array_equal(k[1:] >> np.uint64(2), k[:-1] & np.uint64((1 << 58) - 1))
+    assert np.array_equal(k[100:], H.kmer_u64(49_900, 2, 60, start=100))
+    # repetitive: far fewer distinct k-mers than keys
+    assert len(np.unique(k)) < 0.8 * len(k)
