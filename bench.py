@@ -398,21 +398,19 @@ def run_ours(args, world, rank, local):
 
     # End to end through the public API with host buffers: every step copies
     # each input from pinned host memory to the device, sorts it and copies the
-    # sorted keys back (Context.sort_host overlaps the copies of neighbouring
+    # sorted keys back (ahs_sort_host overlaps the copies of neighbouring
     # arrays with the sort in between).
     host_in = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in VARIANTS]
     host_out = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in VARIANTS]
     for h, v in zip(host_in, VARIANTS):
         h.copy_(inputs[v])
-    dev_bufs = [(torch.empty(n, dtype=torch.int32, device="cuda"),
-                 torch.empty(n, dtype=torch.int32, device="cuda")) for _ in range(2)]
     torch.cuda.synchronize()
 
     def e2e_step():
-        # Consecutive steps overlap (the next step's first copy in runs during
-        # this step's last copy out); the timed region ends after wait_host.
-        ctx.sort_host(host_in, host_out, key_type=ahs.AHS_U32, stream=stream,
-                      device_buffers=dev_bufs, wait=False)
+        # One C-ABI call (ahs_sort_host) per step; consecutive steps overlap
+        # (the next step's first copy in runs during this step's last copy
+        # out); the timed region ends after ahs_wait_host.
+        ctx.sort_host(host_in, host_out, key_type=ahs.AHS_U32, stream=stream, wait=False)
 
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
@@ -602,11 +600,31 @@ def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    # one more call, traced: per-kernel device time and the host gaps between launches
+    import collections
+    ctx.trace(True)
+    e0.record()
+    ctx.sort_batch(keys, offs_l, out=out, key_type=ahs.AHS_U32)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.trace(False)
+    tr = ctx.trace_collect()
+    kt = collections.defaultdict(lambda: [0, 0.0, 0])
+    for name, items, ms_, _ in tr:
+        kt[name][0] += 1
+        kt[name][1] += ms_
+        kt[name][2] += items
+    busy = sum(x[1] for x in kt.values())
     times_sorted = sorted(times)
     res = {"segments": n_seg, "keys": total, "batched_ms_p50": round(statistics.median(times), 3),
            "batched_ms_p99": round(times_sorted[min(len(times_sorted) - 1, int(0.99 * len(times_sorted)))], 3),
            "batched_gkeys_s": round(total / (statistics.median(times) / 1e3) / 1e9, 3),
-           "seg_per_strategy": {ahs.STRATEGY_NAMES[i]: int(info.seg_per_strategy[i]) for i in range(1, 6)}}
+           "seg_per_strategy": {ahs.STRATEGY_NAMES[i]: int(info.seg_per_strategy[i]) for i in range(1, 6)},
+           "traced_call_ms": round(e0.elapsed_time(e1), 3), "kernel_ms": round(busy, 3),
+           "host_ms": {"features": round(info.ms_features, 3), "select": round(info.ms_select, 3),
+                       "sort": round(info.ms_sort, 3)},
+           "kernels": {k: {"launches": c, "ms": round(m, 3)} for k, (c, m, _) in
+                       sorted(kt.items(), key=lambda kv: -kv[1][1])}}
     if per_array:
         torch.cuda.synchronize()
         e0.record()
@@ -674,10 +692,12 @@ def run_served_segments(device: int, keys, out, offs_l, n_seg: int, budget: int 
 
 def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5,
                pool: int = 48, max_keys: int = 10**8):
-    """Poisson arrivals of uint32 sort requests (sizes log-uniform in
-    [10^3, max_keys], config-4 distributions, keys pre-generated on the device
-    into a pool of input buffers) at an offered load in Gkeys/s, through the
-    serving loop; and the same requests sorted serially one by one."""
+    """Config 5: Poisson arrivals of uint32 sort requests at an offered load
+    in Gkeys/s; request r has a log-uniform size in [10^3, max_keys] and a
+    config-4 shape, and its keys are generated by the library on the device
+    from (seed 5, r) (AHS_REQ_GENERATE) into one of `pool` output buffers;
+    64 GB admission budget.  Against it: the first `pool` requests sorted
+    serially one by one (device time of ahs_sort alone)."""
     import ctypes
     import torch
     import numpy as np
@@ -685,22 +705,10 @@ def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5
     from gen import device as gdev
     from gen import host as gh
     rng = np.random.default_rng(seed)
-    sizes = gh.log_uniform_lengths(pool, seed, 7, 1000, max_keys)
-    types = gh.below32(gh.draws(seed, 8, 0, pool), 4).astype(np.int64)
-    ins = []
-    for i in range(pool):
-        n = int(sizes[i])
-        t = int(types[i])
-        if t == 0:
-            ins.append(gdev.uniform_u32(n, seed, 100 + i, 4096))
-        elif t == 1:
-            ins.append(gdev.zipf_u32(n, seed, 200 + i, 300 + i))
-        elif t == 2:
-            ins.append(gdev.uniform_u32(n, seed, 400 + i, 1 << 32))
-        else:
-            ins.append(gdev.swaps_u32(gdev.sorted_u32(gdev.uniform_u32(n, seed, 500 + i, 1 << 32)),
-                                      n // 100, seed, 600 + i))
-    outs = [torch.empty_like(x) for x in ins]
+    n_max = 1 << 18
+    sizes = gh.log_uniform_lengths(n_max, seed, 7, 1000, max_keys)
+    kinds = gh.below32(gh.draws(seed, 8, 0, n_max), 4).astype(np.int64)
+    outs = [torch.empty(max_keys, dtype=torch.int32, device="cuda") for _ in range(pool)]
     torch.cuda.synchronize()
     mean = float(np.mean(sizes))
     rate = load_gkeys * 1e9 / mean                       # requests per second
@@ -714,13 +722,13 @@ def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5
     submitted = skipped = 0
     while True:
         now = time.perf_counter()
-        if now - t_start >= seconds:
+        if now - t_start >= seconds or submitted >= n_max:
             break
-        # reap finished requests so their buffers can be reused
         still = []
         for tk, i in pending:
             r = ahs.ahs_result_t()
             if ahs.lib.ahs_serve_poll(ctx.handle, tk, 0, ctypes.byref(r)) == ahs.AHS_OK:
+                ahs.check(r.status, "served request")
                 busy[i] = False
             else:
                 still.append((tk, i))
@@ -733,8 +741,11 @@ def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5
         if not free:
             skipped += 1
             continue
-        i = free[int(rng.integers(0, len(free)))]
-        req = ahs.ahs_request_t(ins[i].data_ptr(), outs[i].data_ptr(), ins[i].numel(), ahs.AHS_U32)
+        i = free[0]
+        req = ahs.ahs_request_t()
+        req.d_keys_out, req.n, req.type = outs[i].data_ptr(), int(sizes[submitted]), ahs.AHS_U32
+        req.flags, req.gen_seed, req.gen_id = ahs.AHS_REQ_GENERATE, seed, submitted
+        req.gen_kind = int(kinds[submitted])
         tk = ctypes.c_uint64()
         ahs.check(ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(req), ctypes.byref(tk)), "submit")
         busy[i] = True
@@ -747,21 +758,32 @@ def run_served(ctx_device: int, load_gkeys: float, seconds: float, seed: int = 5
     st = ahs.ahs_serve_stats_t()
     ahs.check(ahs.lib.ahs_serve_stats(ctx.handle, ctypes.byref(st)), "stats")
     ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "stop")
-    # serial per-request baseline: the same pool, one request at a time
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(pool):
-        ctx.sort(ins[i], out=outs[i], key_type=ahs.AHS_U32)
-    torch.cuda.synchronize()
-    serial = float(np.sum(sizes)) / (time.perf_counter() - t0) / 1e9
+    del outs
+    torch.cuda.empty_cache()
+    # serial per-request baseline: the first requests, generated the same way,
+    # each sorted alone (device time of the sort only)
+    stream = torch.cuda.current_stream()
+    serial_ms, serial_keys = 0.0, 0
+    for rid in range(min(pool, max(submitted, 1))):
+        keys = gdev.request_keys(seed, rid, int(kinds[rid]), int(sizes[rid]))
+        out = torch.empty_like(keys)
+        ctx.sort(keys, out=out, key_type=ahs.AHS_U32, stream=stream)   # warm
+        serial_ms += statistics.median(
+            timed_calls(lambda: ctx.sort(keys, out=out, key_type=ahs.AHS_U32, stream=stream), 3, stream))
+        serial_keys += int(sizes[rid])
+        del keys, out
     ctx.close()
+    serial = serial_keys / (serial_ms / 1e3) / 1e9
+    sustained = st.keys / elapsed / 1e9
     return {"offered_gkeys_s": load_gkeys, "seconds": round(elapsed, 2), "submitted": submitted,
             "dropped_no_free_buffer": skipped, "completed": int(st.completed),
-            "sustained_gkeys_s": round(st.keys / elapsed / 1e9, 3),
+            "sustained_gkeys_s": round(sustained, 3),
             "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3),
             "batches": int(st.batches), "peak_reserved_gb": round(st.peak_reserved_bytes / 2**30, 2),
             "serial_per_request_gkeys_s": round(serial, 3),
-            "sizes": "log-uniform [1e3, %d] keys, pool of %d pre-generated requests" % (max_keys, pool)}
+            "served_over_serial": round(sustained / serial, 3),
+            "requests": "log-uniform [1e3, %d] keys, config-4 shapes, keys generated by the library "
+                        "per (seed %d, request id); %d output buffers" % (max_keys, seed, pool)}
 
 
 def run_case(args, local):
@@ -782,7 +804,7 @@ def run_case(args, local):
         kt, w, v = ahs.AHS_U32, 4, 0
     out = torch.empty_like(keys)
     vout = torch.empty_like(vals) if vals is not None else None
-    ctx = ahs.Context(local)
+    ctx = ahs.Context(local, tuning_path=args.tuning if args.tuning else "shipped")
     for _ in range(args.warmup):
         ctx.sort(keys, vals=vals, out=out, vals_out=vout, force=force, key_type=kt)
     torch.cuda.synchronize()
@@ -808,10 +830,15 @@ def run_case(args, local):
         kernels[name] = {"launches": c, "avg_ms": round(t / c, 4),
                          "gbs": round(b / (t / c / 1e3) / 1e9, 1) if b else None,
                          "frac": round(b / (t / c / 1e3) / 1e9 / peak, 4) if b else None}
-    print(json.dumps({"case": args.case, "force": args.force, "n": args.n,
-                      "strategy": ahs.STRATEGY_NAMES[r.strategy], "ms_per_sort": round(ms, 4),
-                      "gkeys_s": round(args.n / (ms / 1e3) / 1e9, 3), "peak_gbs": peak,
-                      "peak_kind": kind, "kernels": kernels}), flush=True)
+    line = {"case": args.case, "force": args.force, "n": args.n,
+            "strategy": ahs.STRATEGY_NAMES[r.strategy], "ms_per_sort": round(ms, 4),
+            "gkeys_s": round(args.n / (ms / 1e3) / 1e9, 3), "peak_gbs": peak,
+            "peak_kind": kind, "kernels": kernels}
+    if args.launches:
+        # every launch of the last call: kernel, keys, device ms, start offset
+        per = len(trace) // max(1, args.steps)
+        line["last_call"] = [(k, it, round(t, 4), round(s0, 4)) for k, it, t, s0 in trace[-per:]]
+    print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -829,6 +856,8 @@ def main():
                    help="diagnostic: one array of config 2 (a-f) or config 3, see --force")
     p.add_argument("--force", choices=["auto", "counting", "radix", "general"], default="auto")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and served sections")
+    p.add_argument("--launches", action="store_true", help="with --case: list the last call's launches")
+    p.add_argument("--tuning", default=None, help="with --case: tuned-shape table to load")
     p.add_argument("--batch-segments", type=int, default=100_000,
                    help="segments of the config-4 batch in the default run")
     p.add_argument("--serve-loads", type=float, nargs="+", default=[2.0, 5.0, 10.0, 40.0],

@@ -4,6 +4,7 @@
 // part of the sorting method.  Built as gen/libahsgen.so, separate from the
 // sorting library.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace {
@@ -128,7 +129,15 @@ __global__ void k_kmer_u64(unsigned long long* out, unsigned long long n, unsign
     }
 }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+__global__ void k_replace_u32(uint32_t* a, unsigned long long n, unsigned long long key_p,
+                              unsigned long long key_v, unsigned long long thresh53) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += stride)
+        if ((draw(key_p, i) >> 11) < thresh53) a[i] = (uint32_t)(draw(key_v, i) >> 32);
+}
+
+__host__ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7FEB352Du;
     x ^= x >> 15;
@@ -263,6 +272,35 @@ int gen_kmer_u64(void* out, unsigned long long n, unsigned long long seed, unsig
                                                       stream_key(seed, stream + 1),
                                                       stream_key(seed, stream + 2), start);
     return (int)cudaGetLastError();
+}
+
+int gen_replace_u32(void* a, unsigned long long n, unsigned long long seed, unsigned long long stream,
+                    unsigned long long thresh53, void* st) {
+    if (n == 0) return 0;
+    k_replace_u32<<<grid(n), 256, 0, (cudaStream_t)st>>>((uint32_t*)a, n, stream_key(seed, stream),
+                                                         stream_key(seed, stream + 1), thresh53);
+    return (int)cudaGetLastError();
+}
+
+// Host-side tables of the Zipf workloads (as gen/host.py zipf_cdf and
+// zipf_values): the fp64 CDF of p_r ~ r^-s by sequential summation in rank
+// order (last entry 1.0), and the distinct values hash32(r ^ k1) ^ k2.
+void gen_zipf_cdf_host(double* out, unsigned nv, double s) {
+    double total = 0.0;
+    for (unsigned r = 1; r <= nv; ++r) total += pow((double)r, -s);
+    double acc = 0.0;
+    for (unsigned r = 1; r <= nv; ++r) {
+        acc += pow((double)r, -s);
+        out[r - 1] = acc / total;
+    }
+    if (nv) out[nv - 1] = 1.0;
+}
+
+void gen_zipf_values_host(uint32_t* out, unsigned long long seed, unsigned long long stream,
+                          unsigned nv) {
+    const unsigned long long k = mix64(stream_key(seed, stream) + kGolden);   // draw 0
+    const uint32_t k1 = (uint32_t)(k & 0xffffffffull), k2 = (uint32_t)(k >> 32);
+    for (unsigned r = 0; r < nv; ++r) out[r] = hash32(r ^ k1) ^ k2;
 }
 
 int gen_batch_u32(void* out, const void* d_offs, const void* d_types, unsigned nseg,

@@ -30,6 +30,7 @@ def lib():
         L.gen_swaps_u32.argtypes = [vp, u64, u64, u64, u64, vp]
         L.gen_batch_u32.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp, ctypes.c_uint, vp]
         L.gen_gaussian_i32.argtypes = [vp, u64, u64, u64, ctypes.c_longlong, u64, vp]
+        L.gen_replace_u32.argtypes = [vp, u64, u64, u64, u64, vp]
         L.gen_kmer_u64.argtypes = [vp, u64, u64, u64, u64, vp]
         L.gen_batch_swaps.argtypes = [vp, vp, vp, ctypes.c_uint, u64, vp]
         _lib = L
@@ -78,6 +79,23 @@ def kmer_u64(n, seed, stream, start=0):
     out = torch.empty(n, dtype=torch.int64, device="cuda")
     _ok(lib().gen_kmer_u64(out.data_ptr(), n, seed, stream, start, _st()))
     return out
+
+
+def replace_u32(a, seed, stream, thresh53=H.REPLACE_1PCT_53):
+    _ok(lib().gen_replace_u32(a.data_ptr(), a.numel(), seed, stream, thresh53, _st()))
+    return a
+
+
+def request_keys(seed, rid, kind, n):
+    """Keys of a library-generated served request (as gen.host.request_keys)."""
+    s0 = H.request_stream(rid, 0)
+    if kind == 0:
+        return uniform_u32(n, seed, s0, 4096)
+    if kind == 1:
+        return zipf_u32(n, seed, H.request_stream(rid, 1), s0)
+    if kind == 2:
+        return uniform_u32(n, seed, s0, 1 << 32)
+    return replace_u32(sorted_u32(uniform_u32(n, seed, s0, 1 << 32)), seed, H.request_stream(rid, 2))
 
 
 def sorted_u32(x):

@@ -262,6 +262,49 @@ def kmer_u64(n: int, seed: int, stream: int, start: int = 0) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Served requests generated by the library (config 5)
+# ----------------------------------------------------------------------------
+
+REPLACE_1PCT_53 = 90071992547410   # P = 0.01 on the 53-bit integer scale
+REQ_KINDS = ("a", "b", "c", "e")   # config-4 shapes, as gen_kind 0..3
+
+
+def replace_u32(a: np.ndarray, seed: int, stream: int, thresh53: int = REPLACE_1PCT_53) -> np.ndarray:
+    """Replace each position with probability thresh53 / 2^53 by a uniform
+    32-bit draw (position-parallel: a nearly sorted shape without a
+    sequential swap chain)."""
+    n = len(a)
+    if n == 0:
+        return a
+    d = draws(seed, stream, 0, n)
+    rep = (d >> U64(11)) < U64(thresh53)
+    v = (draws(seed, stream + 1, 0, n) >> U64(32)).astype(np.uint32)
+    a[rep] = v[rep]
+    return a
+
+
+def request_stream(rid: int, part: int) -> int:
+    """Stream of part `part` of served request `rid` (keys 0, Zipf values 1, replacement 2)."""
+    return (1 << 40) + 4 * rid + part
+
+
+def request_keys(seed: int, rid: int, kind: int, n: int) -> np.ndarray:
+    """The uint32 keys of a library-generated served request (gen_kind 0..3:
+    uniform below 4096; Zipf(1.1) over 1,024 distinct values; uniform 32-bit;
+    sorted uniform 32-bit with 1% of the positions replaced)."""
+    s0 = request_stream(rid, 0)
+    if kind == 0:
+        return uniform_u32(n, seed, s0, 4096)
+    if kind == 1:
+        return zipf_u32(n, seed, request_stream(rid, 1), s0)
+    if kind == 2:
+        return uniform_u32(n, seed, s0, 1 << 32)
+    if kind == 3:
+        return replace_u32(np.sort(uniform_u32(n, seed, s0, 1 << 32)), seed, request_stream(rid, 2))
+    raise ValueError(kind)
+
+
+# ----------------------------------------------------------------------------
 # The workload configurations
 # ----------------------------------------------------------------------------
 

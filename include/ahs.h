@@ -75,10 +75,18 @@ typedef enum {
  *            COUNTING only for k <= 65,536 and SMALL only up to the GB300 n_t
  *            (else GENERAL).  Without a loaded table every n takes the small-n
  *            branch.
- *  CUSTOM:   the thresholds given in ahs_config_t.thresholds. */
+ *  CUSTOM:   the thresholds given in ahs_config_t.thresholds.
+ *  LEMMA32:  Section III-I (Lemma 3.2, Table V), the memory-aware choice for
+ *            large ranges: PAPER's chain up to k_max = 10^6; above it COUNTING
+ *            when k/n < 5 (high density) or when the number of distinct values
+ *            k' is known (ahs_features_t.distinct, from ahs_entropy_exact) and
+ *            k' <= 1000 (skewed, k' << k), RADIX when d < 1 + k/n with d from
+ *            Eq. 4, else GENERAL.  ahs_select returns the paper's pick; an
+ *            AUTO sort runs a COUNTING pick with k > 65,536 on the radix path
+ *            (this library's counting sort reads the <= 2^16-bin histogram). */
 typedef enum {
     AHS_SEL_PAPER = 0, AHS_SEL_LISTING6 = 1, AHS_SEL_GB300 = 2, AHS_SEL_MODEL = 3,
-    AHS_SEL_CUSTOM = 4
+    AHS_SEL_CUSTOM = 4, AHS_SEL_LEMMA32 = 5
 } ahs_select_mode;
 
 /* The state vector of Section III-A with the histogram binning it was taken on.
@@ -88,7 +96,9 @@ typedef enum {
  * (key - min) >> hist_shift, hist_shift = max(0, bitlen(span) - 16); for
  * k <= 65,536 the bins are the key values.  entropy_bits = -sum p log2 p over
  * non-empty bins (fp64), entropy_norm = entropy_bits / log2(nbins) (0 if
- * nbins == 1).  descents = #{i : key[i] > key[i+1]} (0: already in order). */
+ * nbins == 1).  descents = #{i : key[i] > key[i+1]} (0: already in order).
+ * distinct = k', the number of distinct values, when known (ahs_entropy_exact
+ * measures it; the feature pass leaves it 0 = unknown). */
 typedef struct {
     uint64_t n;
     uint64_t min_bits;
@@ -99,6 +109,7 @@ typedef struct {
     double entropy_bits;
     double entropy_norm;
     uint64_t descents;
+    uint64_t distinct;
 } ahs_features_t;
 
 /* FSM thresholds (Section III-A, Table II).  Comparisons follow the text:
@@ -241,6 +252,16 @@ ahs_status ahs_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_ty
 ahs_status ahs_features_noalloc(const void* d_keys, uint64_t n, ahs_key_type type, void* stream,
                                 ahs_features_t* h_out);
 
+/* Exact per-value entropy (Section III-A: H = -sum over the distinct values v
+ * of p_v log2 p_v, p_v = count(v) / n) and the number of distinct values k',
+ * measured on the device: a copy of d_keys is sorted by this library (AUTO
+ * under the context's profile) into a context-owned side buffer, then the
+ * runs of equal keys are measured.  For k <= 65,536 it equals the feature
+ * pass's entropy_bits.  n <= 2^32 - 1 (AHS_ERR_RANGE above).  Synchronises
+ * `stream`; writes *h_entropy and *h_distinct. */
+ahs_status ahs_entropy_exact(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_key_type type,
+                             void* stream, double* h_entropy, uint64_t* h_distinct);
+
 /* ------------------------------------------- Section III-A / III-H: select */
 
 /* Pure host function: the FSM with explicit thresholds. */
@@ -267,6 +288,34 @@ ahs_status ahs_sort(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
                     uint64_t n, ahs_key_type type, ahs_strategy force,
                     void* stream, ahs_sort_info_t* info);
 
+/* One array in host memory for ahs_sort_host: keys (and optionally a uint32
+ * payload) in, sorted keys (and payload) out; outputs may equal inputs. */
+typedef struct {
+    const void* h_keys_in;
+    void* h_keys_out;
+    const uint32_t* h_vals_in;   /* NULL for every array, or for none */
+    uint32_t* h_vals_out;
+    uint64_t n;
+} ahs_host_array_t;
+
+/* Sort `count` arrays that live in host memory, each as ahs_sort would (force,
+ * the context's profile), end to end: the library copies array i + 1 to the
+ * device and array i - 1 back to the host while it sorts array i (three
+ * streams and two device buffer pairs owned by the context, kept between
+ * calls so that consecutive calls overlap too).  Page-locked host buffers
+ * (cudaHostAlloc) let the copies run asynchronously; pageable ones work but
+ * do not overlap.  The work starts after the work queued on `stream` so far.
+ * wait != 0: returns once every output is in host memory.  wait == 0: returns
+ * once everything is queued; ahs_wait_host(ctx, stream) then makes `stream`
+ * wait for it (synchronise that stream before reading the outputs).
+ * strategies (nullable): receives the strategy each array took.  The host
+ * buffers must stay valid until then.  Errors as ahs_sort. */
+ahs_status ahs_sort_host(ahs_ctx* ctx, const ahs_host_array_t* arrays, uint32_t count,
+                         ahs_key_type type, ahs_strategy force, void* stream, int32_t wait,
+                         ahs_strategy* strategies);
+/* Make `stream` wait (on the device) for every ahs_sort_host call so far. */
+ahs_status ahs_wait_host(ahs_ctx* ctx, void* stream);
+
 /* Largest n the one-block shared-memory sort (AHS_SMALL) takes. */
 uint64_t ahs_small_capacity(ahs_key_type type, int32_t has_payload);
 
@@ -288,11 +337,28 @@ typedef struct {
     uint32_t tick_us;            /* scheduler period when idle */
 } ahs_serve_config_t;
 
+/* A served request: n keys of `type`, optionally with a uint32 payload that
+ * is sorted stably with them.  Either the caller's device keys (d_keys_in,
+ * valid until the request completes) or, with AHS_REQ_GENERATE, keys that
+ * the library writes into d_keys_out on the device from (gen_seed, gen_id,
+ * gen_kind) -- uint32 keys only, no payload -- before sorting them in place:
+ *   gen_kind 0: uniform in [0, 4096);  1: Zipf(1.1) over 1,024 distinct
+ *   values;  2: uniform 32-bit;  3: sorted uniform 32-bit with 1% of the
+ *   positions replaced by uniform draws (the seeded generators of the
+ *   library's workload module, streams 2^40 + 4 gen_id + part). */
+#define AHS_REQ_GENERATE 1u
 typedef struct {
-    const void* d_keys_in;       /* device keys, valid until the request completes */
+    const void* d_keys_in;       /* device keys (unused with AHS_REQ_GENERATE) */
     void* d_keys_out;            /* device output (may equal d_keys_in) */
     uint64_t n;
     ahs_key_type type;
+    uint32_t flags;              /* AHS_REQ_* */
+    const uint32_t* d_vals_in;   /* optional payload (NULL: keys only) */
+    uint32_t* d_vals_out;        /* payload output (may equal d_vals_in) */
+    uint64_t gen_seed;
+    uint64_t gen_id;
+    uint32_t gen_kind;
+    uint32_t reserved;
 } ahs_request_t;
 
 typedef struct {

@@ -110,6 +110,8 @@ def open_library(path: str):
     L.orc_features.argtypes = [vp, u64, i32, ctypes.POINTER(Features)]
     L.orc_entropy_exact.argtypes = [vp, u64, i32, ctypes.POINTER(ctypes.c_double)]
     L.orc_select.argtypes = [ctypes.POINTER(Features), ctypes.POINTER(Fsm)]
+    L.orc_distinct.argtypes = [vp, u64, i32, ctypes.POINTER(ctypes.c_uint64)]
+    L.orc_select_lemma32.argtypes = [ctypes.POINTER(Features), ctypes.POINTER(Fsm), u64]
     L.orc_radix_passes.argtypes = [u64]
     L.orc_radix_passes.restype = ctypes.c_uint32
     for name in ("orc_insertion_sort", "orc_counting_sort", "orc_radix_sort", "orc_merge_sort"):
@@ -183,6 +185,18 @@ def entropy_exact(keys: np.ndarray) -> float:
     _check(lib().orc_entropy_exact(_ptr(keys), len(keys), _key_type(keys), ctypes.byref(out)),
            "entropy_exact")
     return out.value
+
+
+def distinct(keys: np.ndarray) -> int:
+    keys = np.ascontiguousarray(keys)
+    out = ctypes.c_uint64()
+    _check(lib().orc_distinct(_ptr(keys), len(keys), _key_type(keys), ctypes.byref(out)), "distinct")
+    return out.value
+
+
+def select_lemma32(f: Features, profile: Profile = None, distinct: int = 0) -> int:
+    p = (profile or PAPER).c()
+    return lib().orc_select_lemma32(ctypes.byref(f), ctypes.byref(p), distinct)
 
 
 def select(f: Features, profile: Profile) -> int:

@@ -135,6 +135,21 @@ int orc_entropy_exact(const void* keys, uint64_t n, int t, double* out) {
     return ORC_OK;
 }
 
+/* k' = the number of distinct key values (Table V's k'): sorted copy, runs. */
+int orc_distinct(const void* keys, uint64_t n, int t, uint64_t* out) {
+    if (!out || !valid_type(t)) return ORC_EINVAL;
+    *out = 0;
+    if (n == 0) return ORC_OK;
+    val_t* a = load_all(keys, n, t);
+    if (!a) return ORC_ENOMEM;
+    qsort(a, n, sizeof(val_t), cmp_val);
+    uint64_t k = 1;
+    for (uint64_t i = 1; i < n; ++i) k += a[i] != a[i - 1];
+    free(a);
+    *out = k;
+    return ORC_OK;
+}
+
 /* ------------------------------------- Section III-A, Listing 6: the decision FSM */
 
 int orc_select(const orc_features_t* f, const orc_fsm_t* p) {
@@ -147,6 +162,25 @@ int orc_select(const orc_features_t* f, const orc_fsm_t* p) {
     if (k > (uval_t)p->k_max && (!p->use_entropy || f->entropy_norm < p->h_max))
         return ORC_RADIX;                                        /* k > 10^6, H < 0.7 log2 k */
     return ORC_GENERAL;                                          /* quicksort */
+}
+
+/* Section III-I, Lemma 3.2 and Table V: for large ranges (k > k_max) the
+ * memory-aware choice -- counting when k/n < 5 (high density) or when the
+ * distinct values are few (k' <= k_t, "k' << k"; distinct = 0 when unknown),
+ * radix when d < 1 + k/n with d from Eq. 4, else the general sort.  Below
+ * k_max the FSM of Section III-A decides. */
+int orc_select_lemma32(const orc_features_t* f, const orc_fsm_t* p, uint64_t distinct) {
+    if (f->n <= 1) return ORC_IDENTITY;
+    if (f->n <= p->n_t) return ORC_SMALL;
+    if (f->span == 0) return ORC_IDENTITY;
+    uval_t k = (uval_t)f->span + 1, n = (uval_t)f->n;
+    if (k <= (uval_t)p->k_t) return ORC_COUNTING;
+    if (k <= (uval_t)p->k_max) return ORC_GENERAL;
+    if (k < 5 * n) return ORC_COUNTING;                          /* k / n < 5 */
+    if (distinct != 0 && distinct <= p->k_t) return ORC_COUNTING;  /* k' << k */
+    uval_t d = orc_radix_passes(f->span);
+    if (k > (d - 1) * n) return ORC_RADIX;                      /* d < 1 + k / n */
+    return ORC_GENERAL;
 }
 
 /* Eq. 4: d = ceil(log_256 k), computed by repeated division. */

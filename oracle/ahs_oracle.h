@@ -61,6 +61,14 @@ int orc_entropy_exact(const void* keys, uint64_t n, int key_type, double* out);
 
 int orc_select(const orc_features_t* f, const orc_fsm_t* p);
 
+/* k' = the number of distinct key values. */
+int orc_distinct(const void* keys, uint64_t n, int key_type, uint64_t* out);
+
+/* Section III-I (Lemma 3.2, Table V): the memory-aware choice for k > k_max
+ * (counting for k/n < 5 or k' <= k_t, radix for d < 1 + k/n, else general);
+ * the FSM's rules at and below k_max.  distinct = k', 0 if unknown. */
+int orc_select_lemma32(const orc_features_t* f, const orc_fsm_t* p, uint64_t distinct);
+
 /* Radix passes of base 256 over k values: d = ceil(log_256 k) (Eq. 4). */
 uint32_t orc_radix_passes(uint64_t span);
 

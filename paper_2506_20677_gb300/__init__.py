@@ -24,7 +24,7 @@ AHS_OK, AHS_ERR_INVALID_ARG, AHS_ERR_DTYPE, AHS_ERR_OOM, AHS_ERR_BUDGET, AHS_ERR
     AHS_ERR_RANGE = range(11)
 AHS_U32, AHS_U64, AHS_I32, AHS_I64 = range(4)
 AHS_AUTO, AHS_IDENTITY, AHS_SMALL, AHS_COUNTING, AHS_RADIX, AHS_GENERAL = range(6)
-AHS_SEL_PAPER, AHS_SEL_LISTING6, AHS_SEL_GB300, AHS_SEL_MODEL, AHS_SEL_CUSTOM = range(5)
+AHS_SEL_PAPER, AHS_SEL_LISTING6, AHS_SEL_GB300, AHS_SEL_MODEL, AHS_SEL_CUSTOM, AHS_SEL_LEMMA32 = range(6)
 AHS_DEBUG_STALL_ONE_TILE = 1
 STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL")
 
@@ -34,7 +34,7 @@ class ahs_features_t(ctypes.Structure):
                 ("max_bits", ctypes.c_uint64), ("span", ctypes.c_uint64),
                 ("hist_shift", ctypes.c_uint32), ("nbins", ctypes.c_uint32),
                 ("entropy_bits", ctypes.c_double), ("entropy_norm", ctypes.c_double),
-                ("descents", ctypes.c_uint64)]
+                ("descents", ctypes.c_uint64), ("distinct", ctypes.c_uint64)]
 
 
 class ahs_thresholds_t(ctypes.Structure):
@@ -72,7 +72,13 @@ class ahs_serve_config_t(ctypes.Structure):
 
 class ahs_request_t(ctypes.Structure):
     _fields_ = [("d_keys_in", ctypes.c_void_p), ("d_keys_out", ctypes.c_void_p),
-                ("n", ctypes.c_uint64), ("type", ctypes.c_int)]
+                ("n", ctypes.c_uint64), ("type", ctypes.c_int), ("flags", ctypes.c_uint32),
+                ("d_vals_in", ctypes.c_void_p), ("d_vals_out", ctypes.c_void_p),
+                ("gen_seed", ctypes.c_uint64), ("gen_id", ctypes.c_uint64),
+                ("gen_kind", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+AHS_REQ_GENERATE = 1
 
 
 class ahs_result_t(ctypes.Structure):
@@ -84,6 +90,12 @@ class ahs_serve_stats_t(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("keys", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("peak_reserved_bytes", ctypes.c_uint64), ("batches", ctypes.c_uint64)]
+
+
+class ahs_host_array_t(ctypes.Structure):
+    _fields_ = [("h_keys_in", ctypes.c_void_p), ("h_keys_out", ctypes.c_void_p),
+                ("h_vals_in", ctypes.c_void_p), ("h_vals_out", ctypes.c_void_p),
+                ("n", ctypes.c_uint64)]
 
 
 class ahs_trace_entry_t(ctypes.Structure):
@@ -109,12 +121,17 @@ SIGNATURES = {
     "ahs_trace_collect": (ctypes.c_int, [_ctx, _P(ahs_trace_entry_t), _u32, _P(_u32)]),
     "ahs_features": (ctypes.c_int, [_ctx, _vp, _u64, ctypes.c_int, _vp, _P(ahs_features_t)]),
     "ahs_features_noalloc": (ctypes.c_int, [_vp, _u64, ctypes.c_int, _vp, _P(ahs_features_t)]),
+    "ahs_entropy_exact": (ctypes.c_int, [_ctx, _vp, _u64, ctypes.c_int, _vp, _P(ctypes.c_double),
+                                         _P(_u64)]),
     "ahs_select_fsm": (ctypes.c_int, [_P(ahs_features_t), _P(ahs_thresholds_t), _P(ctypes.c_int)]),
     "ahs_select": (ctypes.c_int, [_ctx, _P(ahs_features_t), ctypes.c_int, _u32, _i32,
                                   _P(ctypes.c_int)]),
     "ahs_sort": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _u64, ctypes.c_int, ctypes.c_int, _vp,
                                 _P(ahs_sort_info_t)]),
     "ahs_small_capacity": (_u64, [ctypes.c_int, _i32]),
+    "ahs_sort_host": (ctypes.c_int, [_ctx, _P(ahs_host_array_t), _u32, ctypes.c_int, ctypes.c_int,
+                                     _vp, _i32, _P(ctypes.c_int)]),
+    "ahs_wait_host": (ctypes.c_int, [_ctx, _vp]),
     "ahs_sort_batch": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _P(_u64), _u32, ctypes.c_int,
                                       _vp, _P(ahs_batch_info_t)]),
     "ahs_serve_start": (ctypes.c_int, [_ctx, _P(ahs_serve_config_t)]),
@@ -223,11 +240,6 @@ class Context:
         self.device = device
 
     def close(self):
-        hp = getattr(self, "_hp", None)
-        if hp is not None:   # sort_host's streams may still use its buffers
-            for k in ("sort", "out", "in"):
-                hp[k].synchronize()
-            self._hp = None
         if self.handle:
             lib.ahs_destroy(self.handle)
             self.handle = ctypes.c_void_p()
@@ -280,6 +292,15 @@ class Context:
                                        ctypes.byref(p), ctypes.byref(b)), "ahs_tuned_radix_bits")
         return p.value, b.value
 
+    def entropy_exact(self, keys, key_type=None, stream=None):
+        """(H over every distinct value, number of distinct values), on the device."""
+        h, k = ctypes.c_double(), ctypes.c_uint64()
+        kt = key_type_of(keys) if key_type is None else key_type
+        check(lib.ahs_entropy_exact(self.handle, ctypes.c_void_p(keys.data_ptr()), keys.numel(), kt,
+                                    _stream_handle(stream), ctypes.byref(h), ctypes.byref(k)),
+              "ahs_entropy_exact", self.handle)
+        return h.value, k.value
+
     def select(self, f: ahs_features_t, mode: int, key_bytes: int = 4, has_payload: bool = False):
         out = ctypes.c_int()
         check(lib.ahs_select(self.handle, ctypes.byref(f), mode, key_bytes, int(has_payload),
@@ -305,105 +326,39 @@ class Context:
         return SortResult(out, vals_out, info.strategy, info)
 
     def sort_host(self, host_keys, host_out, key_type=None, force: int = AHS_AUTO,
-                  stream=None, device_buffers=None, wait: bool = True):
-        """Sort a sequence of host arrays (pinned, for asynchronous copies) into
-        the matching host outputs, overlapping the copy of array i + 1 to the
-        device and of array i - 1 back with the sort of array i.  Each array is
-        sorted on its own by ahs_sort.  device_buffers: optional pair of
-        (keys, out) device tensor pairs large enough for every array (reused
-        across calls).  The copy and sort streams and the buffers' events
-        persist in the context, so consecutive calls also overlap: the next
-        call's first copy in waits only for the buffer it reuses.
-
-        wait=True: `stream` (default: the current stream) waits for the whole
-        call.  wait=False: it waits only for this call's start; call
-        wait_host(stream) before reading host_out.  Returns the strategies."""
-        import torch
-        if len(host_out) != len(host_keys) or any(
+                  stream=None, wait: bool = True, host_vals=None, host_vals_out=None):
+        """Sort a sequence of host arrays (torch CPU tensors, pinned for
+        asynchronous copies) into the matching host outputs through
+        ahs_sort_host: the library copies array i + 1 in and array i - 1 out
+        while it sorts array i.  wait=False: returns once queued; call
+        wait_host(stream) and synchronise before reading host_out.  Returns
+        the strategy of each array."""
+        n = len(host_keys)
+        if len(host_out) != n or any(
                 h.dtype != host_keys[0].dtype or o.dtype != h.dtype or o.numel() != h.numel()
                 for h, o in zip(host_keys, host_out)):
             raise AhsError(AHS_ERR_INVALID_ARG, "sort_host: one dtype, matching output sizes")
-        dev = torch.device("cuda", self.device)
-        cap = max((h.numel() for h in host_keys), default=0)
-        caller = stream if stream is not None else torch.cuda.current_stream(dev)
-        hp = self._host_pipe(dev, host_keys[0].dtype if host_keys else torch.int32, cap,
-                             device_buffers)
-        # The caller's earlier work (which may produce the host inputs) comes first.
-        entry = torch.cuda.Event()
-        entry.record(caller)
-        hp["in"].wait_event(entry)
-        hp["sort"].wait_event(entry)
-        bufs, ev = hp["bufs"], hp["ev"]
-        first = hp["turn"]
-        picks = []
-
-        def load(i):
-            b = (first + i) % 2
-            with torch.cuda.stream(hp["in"]):
-                hp["in"].wait_event(ev["consumed"][b])    # the last sort that read buffer b
-                k = bufs[b][0][: host_keys[i].numel()]
-                k.copy_(host_keys[i], non_blocking=True)
-                ev["loaded"][b].record(hp["in"])
-
-        if host_keys:
-            load(0)
-        for i in range(len(host_keys)):
-            b = (first + i) % 2
-            if i + 1 < len(host_keys):
-                load(i + 1)
-            m = host_keys[i].numel()
-            k, o = bufs[b][0][:m], bufs[b][1][:m]
-            hp["sort"].wait_event(ev["loaded"][b])
-            hp["sort"].wait_event(ev["freed"][b])       # the last copy out of buffer b
-            r = self.sort(k, out=o, force=force, key_type=key_type, stream=hp["sort"])
-            ev["consumed"][b].record(hp["sort"])
-            picks.append(r.strategy)
-            with torch.cuda.stream(hp["out"]):
-                hp["out"].wait_event(ev["consumed"][b])
-                host_out[i].copy_(o, non_blocking=True)
-                ev["freed"][b].record(hp["out"])
-        hp["turn"] = (first + len(host_keys)) % 2
-        if wait:
-            self.wait_host(caller)
-        return picks
+        if n == 0:
+            return []
+        kt = key_type_of(host_keys[0]) if key_type is None else key_type
+        arr = (ahs_host_array_t * n)()
+        for i in range(n):
+            arr[i].h_keys_in = host_keys[i].data_ptr()
+            arr[i].h_keys_out = host_out[i].data_ptr()
+            arr[i].n = host_keys[i].numel()
+            if host_vals is not None:
+                arr[i].h_vals_in = host_vals[i].data_ptr()
+                arr[i].h_vals_out = host_vals_out[i].data_ptr()
+        picks = (ctypes.c_int * n)()
+        check(lib.ahs_sort_host(self.handle, arr, n, kt, force, _stream_handle(stream), int(wait),
+                                picks), "ahs_sort_host", self.handle)
+        self._host_refs = (host_keys, host_out, host_vals, host_vals_out)   # alive until waited on
+        return list(picks)
 
     def wait_host(self, stream=None):
         """Make `stream` (default: the current stream) wait for every
         sort_host call issued so far."""
-        import torch
-        hp = getattr(self, "_hp", None)
-        if hp is None:
-            return
-        caller = stream if stream is not None else torch.cuda.current_stream(hp["dev"])
-        for k in ("sort", "out", "in"):
-            caller.wait_stream(hp[k])
-
-    def _host_pipe(self, dev, dtype, cap, device_buffers):
-        """The persistent streams, per-buffer events and device buffers of sort_host."""
-        import torch
-        hp = getattr(self, "_hp", None)
-        if device_buffers is not None:
-            bufs = device_buffers
-        elif hp is not None and hp["bufs"][0][0].dtype == dtype and hp["bufs"][0][0].numel() >= cap:
-            bufs = hp["bufs"]
-        else:
-            bufs = [(torch.empty(cap, dtype=dtype, device=dev), torch.empty(cap, dtype=dtype, device=dev))
-                    for _ in range(2)]
-        if hp is None:
-            hp = {"dev": dev, "turn": 0,
-                  "sort": torch.cuda.Stream(dev), "in": torch.cuda.Stream(dev),
-                  "out": torch.cuda.Stream(dev),
-                  "ev": {k: [torch.cuda.Event(), torch.cuda.Event()]
-                         for k in ("loaded", "consumed", "freed")},
-                  "bufs": bufs}
-            self._hp = hp
-        elif not (hp["bufs"] is bufs or all(
-                x.data_ptr() == y.data_ptr() for p, q in zip(hp["bufs"], bufs) for x, y in zip(p, q))):
-            # New buffers: the old ones may still be in use by earlier calls.
-            for k in ("sort", "out", "in"):
-                hp[k].synchronize()
-            hp["bufs"] = bufs
-        return hp
+        check(lib.ahs_wait_host(self.handle, _stream_handle(stream)), "ahs_wait_host", self.handle)
 
     def sort_batch(self, keys, seg_offsets, out=None, vals=None, vals_out=None, key_type=None,
                    stream=None):

@@ -23,7 +23,10 @@ def _nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    # The library links the workload module's device generators, which it
+    # runs for served requests whose keys it generates itself.
+    own = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    return own + [os.path.join(ROOT, "gen", "device.cu")]
 
 
 def _headers_mtime() -> float:
@@ -38,7 +41,7 @@ def _flags():
 
 
 def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    obj = os.path.join(BUILD, os.path.basename(os.path.dirname(src)) + "_" + os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj
     cmd = [_nvcc(), *ARCH, *_flags(), "-c", src, "-o", obj + ".tmp"]

@@ -134,6 +134,10 @@ ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_by
     case AHS_SEL_CUSTOM:
         s = select_fsm(f, ctx->custom);
         break;
+    case AHS_SEL_LEMMA32:
+        profile_thresholds(AHS_SEL_LEMMA32, &t);
+        s = select_lemma32(f, t);
+        break;
     default:
         profile_thresholds(ctx->cfg.select_mode, &t);
         s = select_fsm(f, t);
@@ -142,6 +146,10 @@ ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_by
     // Insertion-sort sized inputs run in one CTA; a profile whose n_t exceeds
     // that capacity sends the rest to the general path.
     if (s == AHS_SMALL && f.n > blocksort_capacity(key_bytes, payload)) s = AHS_GENERAL;
+    // The counting sort reads the feature histogram (k <= 2^16): a counting
+    // pick over a wider range runs the radix path, whose partition sizes are
+    // the counts of the leading 16 bits.
+    if (s == AHS_COUNTING && f.span >= kMaxBinsCounting) s = AHS_RADIX;
     return s;
 }
 
@@ -310,7 +318,7 @@ void ahs_default_config(ahs_config_t* cfg) {
 }
 
 ahs_status ahs_profile_thresholds(ahs_select_mode mode, ahs_thresholds_t* out) {
-    if (mode == AHS_SEL_CUSTOM) return AHS_ERR_INVALID_ARG;
+    if (mode == AHS_SEL_CUSTOM || mode == AHS_SEL_LEMMA32) return AHS_ERR_INVALID_ARG;
     return profile_thresholds(mode, out);
 }
 
@@ -338,7 +346,7 @@ ahs_status ahs_create(ahs_ctx** out, const ahs_config_t* cfg) {
     if (!ctx) return AHS_ERR_OOM;
     if (cfg) ctx->cfg = *cfg;
     else ahs_default_config(&ctx->cfg);
-    if (ctx->cfg.select_mode < AHS_SEL_PAPER || ctx->cfg.select_mode > AHS_SEL_CUSTOM) {
+    if (ctx->cfg.select_mode < AHS_SEL_PAPER || ctx->cfg.select_mode > AHS_SEL_LEMMA32) {
         delete ctx;
         return AHS_ERR_INVALID_ARG;
     }
@@ -407,6 +415,7 @@ void ahs_destroy(ahs_ctx* ctx) {
     }
     if (ctx->serve) ahs_serve_stop(ctx);
     cudaSetDevice(ctx->device);
+    if (ctx->host_pipe) destroy_host_pipe(ctx->host_pipe);
     cudaDeviceSynchronize();
     for (auto& ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
@@ -518,6 +527,10 @@ ahs_status ahs_select(const ahs_ctx* ctx, const ahs_features_t* f, ahs_select_mo
         return AHS_OK;
     case AHS_SEL_CUSTOM:
         *out = select_fsm(*f, ctx->custom);
+        return AHS_OK;
+    case AHS_SEL_LEMMA32:
+        profile_thresholds(AHS_SEL_LEMMA32, &t);
+        *out = select_lemma32(*f, t);
         return AHS_OK;
     default:
         if (profile_thresholds(mode, &t) != AHS_OK) return AHS_ERR_INVALID_ARG;

@@ -16,6 +16,8 @@
 
 namespace ahs {
 struct ServeState;   // serve.cpp
+struct HostPipe;     // host_sort.cu
+void destroy_host_pipe(HostPipe* p);
 }
 
 struct ahs_ctx {
@@ -51,6 +53,7 @@ struct ahs_ctx {
     ahs::Tracer tracer;
 
     ahs::ServeState* serve = nullptr;   // owned; released by ahs_serve_stop
+    ahs::HostPipe* host_pipe = nullptr; // ahs_sort_host's streams and buffers (owned)
 };
 
 namespace ahs {

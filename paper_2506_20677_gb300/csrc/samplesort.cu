@@ -45,7 +45,7 @@ constexpr uint32_t kMaxLevels = 16;
 constexpr uint32_t kCopyChunk = 4096;           // keys one CTA copies of an unsorted bucket
 constexpr int kSplit = 0;                       // bucket = splitter interval / equality
 constexpr int kDigit = 1;                       // bucket = 8-bit digit of key - segment min
-constexpr int kRange = 2;                       // bucket = number of splitters below the key
+constexpr int kTable = 3;                       // bucket = table[(key - min) >> shift] (histogram bin)
 constexpr int kHistCopies = 4;
 static_assert(kThreads % 32 == 0 && kThreads >= 32, "whole warps");
 static_assert((uint32_t)kThreads * kIpt >= kSamples, "one CTA must hold the whole splitter sample");
@@ -100,14 +100,15 @@ struct Classifier {
     uint32_t m;
     K mn;
     uint32_t shift;
+    const uint8_t* table;   // kTable: bucket of each histogram bin
     __device__ __forceinline__ uint32_t operator()(K o) const {
         if constexpr (MODE == kSplit) {
             return classify_split(tree, sorted, m, o);
-        } else if constexpr (MODE == kRange) {
-            uint32_t j = 1;
-#pragma unroll
-            for (int l = 0; l < 8; ++l) j = 2 * j + (o > tree[j] ? 1u : 0u);
-            return j - 256;
+        } else if constexpr (MODE == kTable) {
+            // m = the table's size: a key outside the histogram's range (an
+            // input changed since its features were taken) reads no further.
+            const K bin = (K)(o - mn) >> shift;
+            return __ldg(table + (bin < (K)m ? (uint32_t)bin : m - 1));
         } else {
             return (uint32_t)((K)(o - mn) >> shift) & 0xffu;
         }
@@ -449,7 +450,8 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
                 const K* __restrict__ splitters,
                 const uint32_t* __restrict__ nsplit, K flip, uint32_t shift,
                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ err,
-                K* __restrict__ dst2 = nullptr, const uint8_t* __restrict__ dsel = nullptr) {
+                K* __restrict__ dst2 = nullptr, const uint8_t* __restrict__ dsel = nullptr,
+                const uint8_t* __restrict__ table = nullptr) {
     constexpr int IPT = FastCfg<K>::kIpt;
     constexpr uint32_t TILE = FastCfg<K>::kTileKeys;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -462,7 +464,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         if (k >= ntiles) { cp_async_commit(); return; }   // keep one group per issue
         const TileDesc t = tiles ? tiles[k] : tile_of(S.seg, nsegs, k, TILE);
         S.tile[s] = t;
-        constexpr bool kTree = MODE == kSplit || MODE == kRange;
+        constexpr bool kTree = MODE == kSplit;
         issue_run(S.buf[s], src + t.begin, t.size, &S.bar[s], kTree ? kSpBytes : 0u);
         if constexpr (kTree)
             bulk_load(S.sp[s], splitters + (size_t)t.seg * 2 * kSlots, kSpBytes, &S.bar[s]);
@@ -482,6 +484,8 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
     __syncthreads();
 
     Classifier<K, MODE> cls{};
+    cls.table = table;
+    if constexpr (MODE == kTable) cls.m = nsplit ? *nsplit : 1u;   // table size
     uint32_t parity = 0;   // bit s: phase of buffer s's barrier
     for (uint32_t it = 0;; ++it) {
         const uint32_t k = blockIdx.x + it * G;
@@ -495,10 +499,10 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         const SegDesc sg = tiles ? segs[t.seg] : S.seg[t.seg];
         const TileSplit<K> sp(src + t.begin, t.size);
         K* buf = S.buf[s];
-        if constexpr (MODE == kSplit || MODE == kRange) {
+        if constexpr (MODE == kSplit) {
             cls.tree = S.sp[s];
             cls.sorted = S.sp[s] + kSlots;
-            if constexpr (MODE == kSplit) cls.m = nsplit[t.seg];
+            cls.m = nsplit[t.seg];
         } else {
             cls.mn = (K)sg.min_ord;
             cls.shift = shift;
@@ -571,7 +575,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
                 if (AHS_DCHECK(lp < t.size, "fast scatter stage", lp)) {
                     buf[lp] = key[i];
                     // A digit is cheaper to recompute than to stage.
-                    if constexpr (MODE == kSplit || MODE == kRange) S.bid[lp] = (uint16_t)b;
+                    if constexpr (MODE != kDigit) S.bid[lp] = (uint16_t)b;
                 }
             }
         }
@@ -768,9 +772,9 @@ cudaError_t set_attrs() {
     if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kDigit>, sizeof(ScatterSmem<K, VALS>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kSplit>, sizeof(FastSmem<K>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kRange>, sizeof(FastSmem<K>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, true>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kRange, true>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable, true>, sizeof(FastSmem<K>));
     return e;
 }
 
@@ -1008,23 +1012,6 @@ ahs_status upload_msd(ahs_ctx* ctx, Level& L, const std::vector<uint32_t>& curso
     return cuda_status(ctx, e);
 }
 
-// Host: splitter table of one segment for the range classifier (tree[1..255]
-// then the 256 sorted values, padded with the largest value) from up to 255
-// increasing ord-space thresholds: a key o goes to bucket #{t : o > t}.
-template <typename K>
-void range_splitters(const std::vector<K>& thr, K* out) {
-    K sorted[kSlots];
-    for (uint32_t j = 0; j < kSlots; ++j) sorted[j] = j < thr.size() ? thr[j] : ~K(0);
-    out[0] = 0;
-    for (uint32_t j = 1; j < kSlots; ++j) {
-        uint32_t d = 0;
-        while ((2u << d) <= j) ++d;                     // depth of node j
-        const uint32_t p = j - (1u << d);
-        out[j] = sorted[((2 * p + 1) << (7 - d)) - 1];
-    }
-    for (uint32_t j = 0; j < kSlots; ++j) out[kSlots + j] = sorted[j];
-}
-
 // Host: greedy grouping of bins [b0, b1) into at most 256 runs of about
 // `target` keys and at most `max_bins` bins (a bin heavier than the target
 // is a run of its own).  Returns the first bin of every run after the first.
@@ -1121,8 +1108,6 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     std::vector<unsigned long long> binpos(nbins + 1, 0);
     for (uint32_t i = 0; i < nbins; ++i) binpos[i + 1] = binpos[i] + hist[i];
     if (binpos[nbins] != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
-    // Keys of bin >= b are exactly those with ord(x) > thr(b).
-    auto thr = [&](uint32_t b) { return (K)(mn + ((K)b << shift) - 1); };
     // Keys of bins [b0, b1) lie in [bin_lo(b0), bin_lo(b0) + 2^range_bits(b0, b1)).
     auto bin_lo = [&](uint32_t b) { return (unsigned long long)(K)(mn + ((K)b << shift)); };
     auto range_bits = [&](uint32_t b0, uint32_t b1) {
@@ -1133,10 +1118,8 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     // final buckets), sized by upper bounds so that no upload has to wait for
     // an earlier one: the host prepares level 2 while level 1 runs, and the
     // bucket lists while level 2 runs.
-    const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(2 * kSlots * sizeof(K)) +
-                        a256(kCols);
-    const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(256 * kCols * 4) +
-                             a256(256 * 2 * kSlots * sizeof(K)));
+    const size_t capA = a256(sizeof(SegDesc)) + a256(kCols * 4) + a256(kMaxBins) + 256 + a256(kCols);
+    const size_t capB = 2 * (a256(256 * sizeof(SegDesc)) + a256(256 * kCols * 4) + a256(kMaxBins) + 256);
     const size_t class_cap = nbins + n / kCopyChunk + 8;   // entries of one class region
     const size_t class_bytes = a256(class_cap * sizeof(FinalBucket));
     const size_t capC = kBucketClasses * class_bytes;
@@ -1158,10 +1141,11 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         K* dst = nullptr;
         K* dst2 = nullptr;              // buckets whose dsel byte is set go here
         std::vector<uint8_t> dsel;      // per (segment, bucket) cursor; empty: all to dst
+        std::vector<uint32_t> ends;     // last bin + 1 of each segment
     };
     // Lists of `P` into the blob, then its launch (after the blob's copy).
     struct Placed {
-        size_t o_segs, o_cur, o_spl, o_dsel;
+        size_t o_segs, o_cur, o_tbl, o_tbn, o_dsel;
         uint32_t ns, nt;
         uint64_t keys;
     };
@@ -1178,28 +1162,38 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             nt += (uint32_t)ceil_div(sd.size, TK);
         }
         constexpr uint32_t CS = cursor_stride<kDigit>();
-        static_assert(CS == cursor_stride<kRange>(), "one cursor layout for both classifiers");
+        static_assert(CS == cursor_stride<kTable>(), "one cursor layout for both classifiers");
         std::vector<uint32_t> cur(P.segs.size() * CS, 0);
-        std::vector<K> spl;
-        if (!P.digit) spl.resize(P.segs.size() * 2 * kSlots);
+        // Table classifier: the bucket of every bin the pass's segments cover
+        // (segments are disjoint runs of bins, so one table serves them all).
+        std::vector<uint8_t> tbl;
+        if (!P.digit) tbl.assign(nbins, 0);
         Placed pl{};
         for (size_t q = 0; q < P.segs.size(); ++q) {
             const uint32_t first = (uint32_t)P.segs[q].min_ord;   // first bin of the segment
-            std::vector<K> t;
             for (size_t j = 0; j < P.starts[q].size(); ++j) {
                 const uint32_t b = P.starts[q][j];
-                if (!P.digit) t.push_back(thr(b));
                 cur[q * CS + j + 1] = (uint32_t)(binpos[b] - binpos[first]);
             }
-            if (!P.digit) range_splitters<K>(t, spl.data() + q * 2 * kSlots);
+            if (!P.digit) {
+                uint32_t bucket = 0;
+                for (uint32_t b = first, j = 0; b < P.ends[q]; ++b) {
+                    while (j < P.starts[q].size() && P.starts[q][j] <= b) { ++j; ++bucket; }
+                    tbl[b] = (uint8_t)bucket;
+                }
+            }
             pl.keys += P.segs[q].size;
         }
-        // The digit classifier takes the ord value of the segment's first bin.
+        // The digit classifier takes the ord value of the segment's first bin,
+        // the table classifier the bin origin (the input's smallest key).
         for (SegDesc& sd : segs)
-            sd.min_ord = P.digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift)) : 0ull;
+            sd.min_ord = P.digit ? (unsigned long long)(K)(mn + ((K)sd.min_ord << shift))
+                                 : (unsigned long long)mn;
         pl.o_segs = blob.add(segs.data(), segs.size() * sizeof(SegDesc));
         pl.o_cur = blob.add(cur.data(), cur.size() * 4);
-        pl.o_spl = P.digit ? 0 : blob.add(spl.data(), spl.size() * sizeof(K));
+        pl.o_tbl = P.digit ? 0 : blob.add(tbl.data(), tbl.size());
+        const uint32_t tbl_n = nbins;
+        pl.o_tbn = P.digit ? 0 : blob.add(&tbl_n, sizeof(tbl_n));
         pl.o_dsel = P.dsel.empty() ? 0 : blob.add(P.dsel.data(), P.dsel.size());
         pl.ns = (uint32_t)segs.size();
         pl.nt = nt;
@@ -1215,7 +1209,8 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         const SegDesc* d_segs = reinterpret_cast<const SegDesc*>(w + pl.o_segs);
         uint32_t* d_cur = reinterpret_cast<uint32_t*>(aux + window + pl.o_cur);
         TraceScope ts(msd ? "msd_scatter" : "sample_scatter", pl.keys, st);
-        const K* spl = reinterpret_cast<const K*>(w + pl.o_spl);
+        const uint8_t* tbl = P.digit ? nullptr : reinterpret_cast<const uint8_t*>(w + pl.o_tbl);
+        const uint32_t* tbn = P.digit ? nullptr : reinterpret_cast<const uint32_t*>(w + pl.o_tbn);
         const uint8_t* dsel = P.dsel.empty() ? nullptr : reinterpret_cast<const uint8_t*>(w + pl.o_dsel);
         if (P.digit && P.group)
             ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
@@ -1226,13 +1221,13 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
                 P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
                 ctx->d_err, P.dst2, dsel);
         else if (P.group)
-            ss_scatter_keys<K, kRange, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err,
-                P.dst2, dsel);
+            ss_scatter_keys<K, kTable, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, tbn, flip, shift, d_cur,
+                ctx->d_err, P.dst2, dsel, tbl);
         else
-            ss_scatter_keys<K, kRange><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, spl, nullptr, flip, 0, d_cur, ctx->d_err,
-                P.dst2, dsel);
+            ss_scatter_keys<K, kTable><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, tbn, flip, shift, d_cur,
+                ctx->d_err, P.dst2, dsel, tbl);
         return cudaGetLastError();
     };
 
@@ -1257,6 +1252,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         Pass P1;
         P1.segs.push_back({0ull, (uint32_t)n, 0ull});
         P1.starts.push_back(s1);
+        P1.ends.push_back(nbins);
         P1.digit = blocks;
         P1.dshift = shift + 8;
         // Probability that two random keys share a level-1 bucket.
@@ -1325,6 +1321,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         split2[g] = (int32_t)((single ? 0u : 1u << 30) | (uint32_t)P.segs.size());
         P.segs.push_back({binpos[b0], (uint32_t)sz, (unsigned long long)b0});
         P.starts.push_back(std::move(st2));
+        P.ends.push_back(b1);
     }
     {
         Blob B{stage + capA, capB};

@@ -27,6 +27,8 @@ ahs_status profile_thresholds(ahs_select_mode mode, ahs_thresholds_t* t) {
     case AHS_SEL_LISTING6:
         t->use_entropy = 0;
         return AHS_OK;
+    case AHS_SEL_LEMMA32:
+        return AHS_OK;   // its rules above k_max are not thresholds
     case AHS_SEL_GB300:
     case AHS_SEL_MODEL:
         // Eq. 2 sizes k_max from the cache a thread owns; on this GPU the
@@ -54,6 +56,29 @@ ahs_strategy select_fsm(const ahs_features_t& f, const ahs_thresholds_t& p) {
     if (p.k_t >= 1 && f.span <= p.k_t - 1) return AHS_COUNTING;
     if (f.span >= p.k_max && (!p.use_entropy || f.entropy_norm < p.h_max)) return AHS_RADIX;
     return AHS_GENERAL;
+}
+
+ahs_strategy select_lemma32(const ahs_features_t& f, const ahs_thresholds_t& p) {
+    using u128 = unsigned __int128;
+    if (f.n <= 1) return AHS_IDENTITY;
+    if (f.n <= p.n_t) return AHS_SMALL;
+    if (f.span == 0) return AHS_IDENTITY;
+    const u128 k = (u128)f.span + 1, n = f.n;
+    if (k <= p.k_t) return AHS_COUNTING;
+    if (k <= p.k_max) return AHS_GENERAL;
+    // Table V: high density (k / n < 5) and skewed ranges (few distinct
+    // values, k' << k, taken as k' <= k_t) are counted.
+    if (k < 5 * n) return AHS_COUNTING;
+    if (f.distinct != 0 && f.distinct <= p.k_t) return AHS_COUNTING;
+    // Lemma 3.2: radix when its d passes cost less space than counting's
+    // n + k, i.e. d < 1 + k / n, with d = ceil(log_256 k) (Eq. 4).
+    u128 reach = 1;
+    uint32_t d = 0;
+    while (reach < k) {
+        reach <<= 8;
+        ++d;
+    }
+    return (u128)(d - 1) * n < k ? AHS_RADIX : AHS_GENERAL;
 }
 
 // ------------------------------------------------------------ tree ensemble

@@ -21,6 +21,8 @@ constexpr uint64_t kMaxBinsCounting = 65536;
 
 ahs_status profile_thresholds(ahs_select_mode mode, ahs_thresholds_t* t);
 ahs_strategy select_fsm(const ahs_features_t& f, const ahs_thresholds_t& p);
+// Section III-I: Lemma 3.2 and Table V above k_max, the FSM's chain below.
+ahs_strategy select_lemma32(const ahs_features_t& f, const ahs_thresholds_t& p);
 
 class TreeModel {
 public:

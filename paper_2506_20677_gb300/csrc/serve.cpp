@@ -26,6 +26,22 @@
 #include "ctx.h"
 #include "internal.h"
 
+// The workload module's device generators (linked into the library), used for
+// requests whose keys the library generates (AHS_REQ_GENERATE).
+extern "C" {
+int gen_uniform_u32(void* out, unsigned long long n, unsigned long long seed,
+                    unsigned long long stream, unsigned long long m, unsigned long long start,
+                    void* st);
+int gen_zipf_u32(void* out, unsigned long long n, unsigned long long seed, unsigned long long stream,
+                 const void* d_cdf, const void* d_values, unsigned nv, unsigned long long start,
+                 void* st);
+int gen_replace_u32(void* a, unsigned long long n, unsigned long long seed, unsigned long long stream,
+                    unsigned long long thresh53, void* st);
+void gen_zipf_cdf_host(double* out, unsigned nv, double s);
+void gen_zipf_values_host(uint32_t* out, unsigned long long seed, unsigned long long stream,
+                          unsigned nv);
+}
+
 namespace ahs {
 ahs_status run_batch(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin, uint32_t* vout,
                      const uint64_t* offs, uint32_t n_seg, KeyDesc kd, cudaStream_t st,
@@ -45,16 +61,81 @@ struct Request {
     uint64_t reserve;
     clock::time_point submitted, admitted;
     bool large;
+    bool payload() const { return req.d_vals_in != nullptr; }
+    const void* keys_src() const {
+        return (req.flags & AHS_REQ_GENERATE) ? req.d_keys_out : req.d_keys_in;
+    }
 };
+
+// Generated requests: Zipf(1.1) over 1,024 values, 1% replacements.
+constexpr unsigned kGenZipfValues = 1024;
+constexpr double kGenZipfS = 1.1;
+constexpr unsigned long long kGenReplace53 = 90071992547410ull;
+unsigned long long gen_stream(uint64_t id, unsigned part) { return (1ull << 40) + 4ull * id + part; }
+
+// Per-lane generator tables: the Zipf CDF (constant) and one request's values.
+struct LaneGen {
+    double* d_cdf = nullptr;
+    uint32_t* d_vals = nullptr;
+    uint32_t* h_vals = nullptr;   // pinned
+    ~LaneGen() {
+        if (d_cdf) cudaFree(d_cdf);
+        if (h_vals) cudaFreeHost(h_vals);
+    }
+    cudaError_t init() {
+        if (d_cdf) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&d_cdf, kGenZipfValues * (sizeof(double) + sizeof(uint32_t)));
+        if (e != cudaSuccess) return e;
+        d_vals = reinterpret_cast<uint32_t*>(d_cdf + kGenZipfValues);
+        e = cudaHostAlloc(&h_vals, kGenZipfValues * sizeof(double), cudaHostAllocDefault);
+        if (e != cudaSuccess) return e;
+        gen_zipf_cdf_host(reinterpret_cast<double*>(h_vals), kGenZipfValues, kGenZipfS);
+        e = cudaMemcpy(d_cdf, h_vals, kGenZipfValues * sizeof(double), cudaMemcpyHostToDevice);
+        return e;
+    }
+};
+
+// Write a generated request's keys into its output buffer (sorted in place
+// afterwards).  Kind 3 sorts uniform keys with the lane's context first.
+ahs_status generate_keys(ahs_ctx* c, const ahs_request_t& r, cudaStream_t st, LaneGen& g) {
+    cudaError_t e = g.init();
+    if (e != cudaSuccess) return cuda_status(c, e);
+    const unsigned long long n = r.n, seed = r.gen_seed;
+    const unsigned long long s0 = gen_stream(r.gen_id, 0);
+    int rc = 0;
+    switch (r.gen_kind) {
+    case 0: rc = gen_uniform_u32(r.d_keys_out, n, seed, s0, 4096, 0, st); break;
+    case 1:
+        gen_zipf_values_host(g.h_vals, seed, gen_stream(r.gen_id, 1), kGenZipfValues);
+        e = cudaMemcpyAsync(g.d_vals, g.h_vals, kGenZipfValues * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // h_vals is reused next
+        if (e != cudaSuccess) return cuda_status(c, e);
+        rc = gen_zipf_u32(r.d_keys_out, n, seed, s0, g.d_cdf, g.d_vals, kGenZipfValues, 0, st);
+        break;
+    case 2: rc = gen_uniform_u32(r.d_keys_out, n, seed, s0, 1ull << 32, 0, st); break;
+    case 3: {
+        rc = gen_uniform_u32(r.d_keys_out, n, seed, s0, 1ull << 32, 0, st);
+        if (rc) break;
+        ahs_status as = ahs_sort(c, r.d_keys_out, r.d_keys_out, nullptr, nullptr, n, AHS_U32,
+                                 AHS_AUTO, st, nullptr);
+        if (as != AHS_OK) return as;
+        rc = gen_replace_u32(r.d_keys_out, n, seed, gen_stream(r.gen_id, 2), kGenReplace53, st);
+        break;
+    }
+    default: return AHS_ERR_INVALID_ARG;
+    }
+    return rc ? cuda_status(c, (cudaError_t)rc) : AHS_OK;
+}
 
 struct Done {
     ahs_result_t res;
 };
 
 uint64_t reserve_for(const ahs_request_t& r) {
-    const uint64_t w = (r.type == AHS_U32 || r.type == AHS_I32) ? 4 : 8;
-    // Temporary keys + partition metadata (about n/4 bytes) + a fixed part;
-    // batched requests also occupy the staging arena (in + out).
+    const uint64_t w = ((r.type == AHS_U32 || r.type == AHS_I32) ? 4 : 8) + (r.d_vals_in ? 4 : 0);
+    // Temporary keys (and payload) + partition metadata (about n/4 bytes) + a
+    // fixed part; batched requests also occupy the staging arena (in + out).
     return r.n * w * 3 + r.n / 4 + (1ull << 20);
 }
 
@@ -83,6 +164,7 @@ struct ServeState {
     // Staging arena of the batch lane (device), grown on demand.
     void* arena = nullptr;
     size_t arena_bytes = 0;
+    LaneGen batch_gen, large_gen;
     std::thread batch_thread, large_thread;
 
     // Move queued requests into the lanes while budget and slots allow (FIFO).
@@ -128,9 +210,12 @@ struct ServeState {
                 r = large_ready.front();
                 large_ready.pop_front();
             }
-            ahs_sort_info_t info;
-            ahs_status st = ahs_sort(large_ctx, r.req.d_keys_in, r.req.d_keys_out, nullptr, nullptr,
-                                     r.req.n, r.req.type, AHS_AUTO, large_stream, &info);
+            ahs_sort_info_t info{};
+            ahs_status st = AHS_OK;
+            if (r.req.flags & AHS_REQ_GENERATE) st = generate_keys(large_ctx, r.req, large_stream, large_gen);
+            if (st == AHS_OK)
+                st = ahs_sort(large_ctx, r.keys_src(), r.req.d_keys_out, r.req.d_vals_in,
+                              r.req.d_vals_out, r.req.n, r.req.type, AHS_AUTO, large_stream, &info);
             std::lock_guard<std::mutex> lk(mu);
             finish_locked(r, st, info.strategy);
             done_cv.notify_all();
@@ -150,11 +235,14 @@ struct ServeState {
                     if (stopping) return;
                     continue;
                 }
-                // Fold every ready request of one key type, up to the arena bound.
+                // Fold every ready request of one key type (with or without a
+                // payload), up to the arena bound.
                 uint64_t nk = 0;
                 const ahs_key_type t = batch_ready.front().req.type;
+                const bool pay = batch_ready.front().payload();
                 for (auto it = batch_ready.begin(); it != batch_ready.end();) {
-                    if (it->req.type == t && (batch.empty() || nk + it->req.n <= kBatchKeys)) {
+                    if (it->req.type == t && it->payload() == pay &&
+                        (batch.empty() || nk + it->req.n <= kBatchKeys)) {
                         nk += it->req.n;
                         batch.push_back(*it);
                         it = batch_ready.erase(it);
@@ -174,10 +262,18 @@ struct ServeState {
 
     ahs_status run_one_batch(const std::vector<Request>& batch) {
         const KeyDesc kd = key_desc(batch[0].req.type);
+        const bool pay = batch[0].payload();
         std::vector<uint64_t> offs(batch.size() + 1, 0);
         for (size_t i = 0; i < batch.size(); ++i) offs[i + 1] = offs[i] + batch[i].req.n;
         const uint64_t n = offs.back();
-        const size_t need = 2 * ((n * kd.bytes + 255) & ~size_t(255));
+        for (const Request& r : batch) {
+            if (!(r.req.flags & AHS_REQ_GENERATE)) continue;
+            const ahs_status gs = generate_keys(batch_ctx, r.req, batch_stream, batch_gen);
+            if (gs != AHS_OK) return gs;
+        }
+        const size_t kbytes = (n * kd.bytes + 255) & ~size_t(255);
+        const size_t vbytes = pay ? ((n * 4 + 255) & ~size_t(255)) : 0;
+        const size_t need = 2 * (kbytes + vbytes);
         if (need > arena_bytes) {
             if (arena) cudaFree(arena);
             arena = nullptr;
@@ -189,19 +285,29 @@ struct ServeState {
             arena_bytes = need + need / 2;
         }
         char* in = static_cast<char*>(arena);
-        char* out = in + ((n * kd.bytes + 255) & ~size_t(255));
+        char* out = in + kbytes;
+        uint32_t* vin = pay ? reinterpret_cast<uint32_t*>(out + kbytes) : nullptr;
+        uint32_t* vout = pay ? reinterpret_cast<uint32_t*>(out + kbytes + vbytes) : nullptr;
         cudaError_t e = cudaSuccess;
-        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i)
-            e = launch_copy32(in + offs[i] * kd.bytes, batch[i].req.d_keys_in,
+        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i) {
+            e = launch_copy32(in + offs[i] * kd.bytes, batch[i].keys_src(),
                               batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
+            if (e == cudaSuccess && pay)
+                e = launch_copy32(vin + offs[i], batch[i].req.d_vals_in, batch[i].req.n,
+                                  batch_ctx->sms, batch_stream);
+        }
         if (e != cudaSuccess) return cuda_status(batch_ctx, e);
         ahs_batch_info_t info;
-        ahs_status st = run_batch(batch_ctx, in, out, nullptr, nullptr, offs.data(),
+        ahs_status st = run_batch(batch_ctx, in, out, vin, vout, offs.data(),
                                   (uint32_t)batch.size(), kd, batch_stream, &info);
         if (st != AHS_OK) return st;
-        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i)
+        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i) {
             e = launch_copy32(batch[i].req.d_keys_out, out + offs[i] * kd.bytes,
                               batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
+            if (e == cudaSuccess && pay)
+                e = launch_copy32(batch[i].req.d_vals_out, vout + offs[i], batch[i].req.n,
+                                  batch_ctx->sms, batch_stream);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(batch_stream);
         return cuda_status(batch_ctx, e);
     }
@@ -248,7 +354,12 @@ ahs_status ahs_serve_submit(ahs_ctx* ctx, const ahs_request_t* req, uint64_t* ti
     ServeState* s = ctx->serve;
     if (!s) return AHS_ERR_INVALID_ARG;
     if (req->type < AHS_U32 || req->type > AHS_I64) return AHS_ERR_DTYPE;
-    if (req->n && (!req->d_keys_in || !req->d_keys_out)) return AHS_ERR_INVALID_ARG;
+    if (req->flags & ~AHS_REQ_GENERATE) return AHS_ERR_INVALID_ARG;
+    const bool gen = (req->flags & AHS_REQ_GENERATE) != 0;
+    if (gen && (req->type != AHS_U32 || req->d_vals_in || req->gen_kind > 3))
+        return AHS_ERR_INVALID_ARG;
+    if (req->n && (!req->d_keys_out || (!gen && !req->d_keys_in))) return AHS_ERR_INVALID_ARG;
+    if (req->n && req->d_vals_in && !req->d_vals_out) return AHS_ERR_INVALID_ARG;
     ahs::Request r{};
     r.req = *req;
     r.reserve = ahs::reserve_for(*req);

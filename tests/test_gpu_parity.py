@@ -276,6 +276,24 @@ def test_sort_host_pipeline(ahs, ctx):
             assert np.array_equal(t.numpy().view(np.uint32), np.sort(a))
 
 
+def test_sort_host_payload_against_oracle(ahs, ctx, orc):
+    """ahs_sort_host with a payload: every array in the unique stable order."""
+    import torch
+    rng = np.random.default_rng(12)
+    arrays = [rng.integers(0, 3000 if i % 2 else 2**32, size=m, dtype=np.uint32)
+              for i, m in enumerate([200_003, 17, (1 << 19) + 1])]
+    vals = [np.arange(len(a), dtype=np.uint32)[::-1].copy() for a in arrays]
+    hk = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in arrays]
+    hv = [torch.from_numpy(v.view(np.int32)).pin_memory() for v in vals]
+    ok = [torch.empty_like(h).pin_memory() for h in hk]
+    ov = [torch.empty_like(h).pin_memory() for h in hv]
+    ctx.sort_host(hk, ok, key_type=ahs.AHS_U32, host_vals=hv, host_vals_out=ov)
+    for a, v, k2, v2 in zip(arrays, vals, ok, ov):
+        ek, ev = orc.merge_sort(a, v)
+        assert np.array_equal(k2.numpy().view(np.uint32), ek)
+        assert np.array_equal(v2.numpy().view(np.uint32), ev)
+
+
 def test_sorted_input_skips_histogram_only_when_identity(ahs, orc):
     """Under GB300 an input in order is returned as it is without its
     histogram (entropy NaN); under PAPER, or when a strategy is forced, the

@@ -123,3 +123,67 @@ def test_budget_refusal_and_admission_bound(ahs):
         res = ahs.ahs_result_t()
         assert ahs.lib.ahs_serve_poll(ctx.handle, 10**9, 0, ctypes.byref(res)) == ahs.AHS_ERR_NOT_FOUND
         ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "serve_stop")
+
+
+def test_generated_requests_against_oracle(ahs):
+    """AHS_REQ_GENERATE: the library writes each request's keys on the device
+    from (seed, id, kind); the same keys come from the host generator, and
+    every result is the oracle's sort of them, alone and in the mix."""
+    import torch
+    seed = 5
+    lengths = gen.log_uniform_lengths(12, 56, 1, 1000, 5_000_000)
+    reqs = [(rid, int(L), rid % 4) for rid, L in enumerate(lengths)]
+    reqs.append((99, 4_500_000, 3))           # large lane, nearly sorted kind
+    with ahs.Context(0) as ctx:
+        _serve(ahs, ctx, budget=16 << 30)
+        outs = [torch.empty(L, dtype=torch.int32, device="cuda") for _, L, _ in reqs]
+        tickets = []
+        for (rid, L, kind), o in zip(reqs, outs):
+            r = ahs.ahs_request_t()
+            r.d_keys_out, r.n, r.type = o.data_ptr(), L, ahs.AHS_U32
+            r.flags, r.gen_seed, r.gen_id, r.gen_kind = ahs.AHS_REQ_GENERATE, seed, rid, kind
+            t = ctypes.c_uint64()
+            ahs.check(ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(r), ctypes.byref(t)), "submit")
+            tickets.append(t.value)
+        for (rid, L, kind), o, t in zip(reqs, outs, tickets):
+            rc, res = _wait(ahs, ctx, t)
+            assert rc == ahs.AHS_OK and res.status == ahs.AHS_OK, rid
+            keys = gen.request_keys(seed, rid, kind, L)
+            assert np.array_equal(host(o, np.uint32), _oracle_sorted(keys)), (rid, kind)
+        # generation needs uint32 keys and no payload
+        bad = ahs.ahs_request_t()
+        bad.d_keys_out, bad.n, bad.type, bad.flags = outs[0].data_ptr(), 10, ahs.AHS_U64, 1
+        t = ctypes.c_uint64()
+        assert ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(bad), ctypes.byref(t)) == \
+            ahs.AHS_ERR_INVALID_ARG
+        ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "serve_stop")
+
+
+def test_payload_requests_stable_against_oracle(ahs):
+    """Served requests with a uint32 payload come back in the unique stable
+    order (the oracle's merge sort), in both lanes."""
+    import torch
+    rng = np.random.default_rng(9)
+    sizes = [1000, 70_001, 300_000, 5_000_000, 2]
+    arrays = [rng.integers(0, 5000 if i % 2 else 2**32, size=n, dtype=np.uint32)
+              for i, n in enumerate(sizes)]
+    with ahs.Context(0) as ctx:
+        _serve(ahs, ctx, budget=8 << 30)
+        bufs, tickets = [], []
+        for a in arrays:
+            v = np.arange(len(a), dtype=np.uint32)
+            ki, ko, vi, vo = dev(a), dev(np.zeros_like(a)), dev(v), dev(np.zeros_like(v))
+            r = ahs.ahs_request_t()
+            r.d_keys_in, r.d_keys_out, r.n, r.type = ki.data_ptr(), ko.data_ptr(), len(a), ahs.AHS_U32
+            r.d_vals_in, r.d_vals_out = vi.data_ptr(), vo.data_ptr()
+            t = ctypes.c_uint64()
+            ahs.check(ahs.lib.ahs_serve_submit(ctx.handle, ctypes.byref(r), ctypes.byref(t)), "submit")
+            bufs.append((ki, ko, vi, vo, v))
+            tickets.append(t.value)
+        for a, (ki, ko, vi, vo, v), t in zip(arrays, bufs, tickets):
+            rc, res = _wait(ahs, ctx, t)
+            assert rc == ahs.AHS_OK and res.status == ahs.AHS_OK
+            ek, ev = oracle.merge_sort(a, v)
+            assert np.array_equal(host(ko, np.uint32), ek)
+            assert np.array_equal(host(vo, np.uint32), ev)
+        ahs.check(ahs.lib.ahs_serve_stop(ctx.handle), "serve_stop")
