@@ -329,6 +329,15 @@ ahs_status ahs_sort_batch(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
                           const uint64_t* h_seg_offsets, uint32_t n_seg,
                           ahs_key_type type, void* stream, ahs_batch_info_t* info);
 
+/* ahs_sort_batch with the n_seg + 1 offsets in device memory (d_seg_offsets,
+ * for batches whose layout is produced on the device).  The offsets are read
+ * back behind the work already queued on `stream`, then the call proceeds as
+ * ahs_sort_batch (same rules and errors).  Synchronises `stream`. */
+ahs_status ahs_sort_batch_dev(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
+                              const uint32_t* d_vals_in, uint32_t* d_vals_out,
+                              const uint64_t* d_seg_offsets, uint32_t n_seg,
+                              ahs_key_type type, void* stream, ahs_batch_info_t* info);
+
 /* -------------------------------------------------------------- serving */
 
 typedef struct {

@@ -134,6 +134,8 @@ SIGNATURES = {
     "ahs_wait_host": (ctypes.c_int, [_ctx, _vp]),
     "ahs_sort_batch": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _P(_u64), _u32, ctypes.c_int,
                                       _vp, _P(ahs_batch_info_t)]),
+    "ahs_sort_batch_dev": (ctypes.c_int, [_ctx, _vp, _vp, _vp, _vp, _vp, _u32, ctypes.c_int,
+                                          _vp, _P(ahs_batch_info_t)]),
     "ahs_serve_start": (ctypes.c_int, [_ctx, _P(ahs_serve_config_t)]),
     "ahs_serve_submit": (ctypes.c_int, [_ctx, _P(ahs_request_t), _P(_u64)]),
     "ahs_serve_poll": (ctypes.c_int, [_ctx, _u64, _i32, _P(ahs_result_t)]),
@@ -368,9 +370,16 @@ class Context:
             out = torch.empty_like(keys)
         if vals is not None and vals_out is None:
             vals_out = torch.empty_like(vals)
-        offs = (ctypes.c_uint64 * len(seg_offsets))(*[int(x) for x in seg_offsets])
         info = ahs_batch_info_t()
         vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        if isinstance(seg_offsets, torch.Tensor) and seg_offsets.is_cuda:
+            # offsets resident on the device (int64 tensor of n_seg + 1)
+            check(lib.ahs_sort_batch_dev(self.handle, vp(keys), vp(out), vp(vals), vp(vals_out),
+                                         vp(seg_offsets), seg_offsets.numel() - 1, kt,
+                                         _stream_handle(stream), ctypes.byref(info)),
+                  "ahs_sort_batch_dev", self.handle)
+            return out, vals_out, info
+        offs = (ctypes.c_uint64 * len(seg_offsets))(*[int(x) for x in seg_offsets])
         check(lib.ahs_sort_batch(self.handle, vp(keys), vp(out), vp(vals), vp(vals_out), offs,
                                  len(seg_offsets) - 1, kt, _stream_handle(stream),
                                  ctypes.byref(info)), "ahs_sort_batch", self.handle)

@@ -52,8 +52,9 @@ def _time(fn, reps, stream):
     return statistics.median(ts)
 
 
-def tune_radix(ctx, n, reps, log):
-    """Best digit width per (key bytes, payload, span bits)."""
+def tune_radix(ctx, n, n_kv, reps, log):
+    """Best digit width per (key bytes, payload, span bits); key-value cases
+    at n_kv keys (the stable passes matter most for large key-value arrays)."""
     import torch
     import paper_2506_20677_gb300 as ahs
     stream = torch.cuda.current_stream()
@@ -75,9 +76,11 @@ def tune_radix(ctx, n, reps, log):
                 lo = -(1 << 63) if span == 64 else 0
                 hi = (1 << 63) - 1 if span == 64 else (1 << span) - 1
                 keys = torch.randint(lo, hi, (n,), device="cuda", dtype=torch.int64, generator=g)
-            vals = torch.arange(n, device="cuda", dtype=torch.int32)
-            out, vout = torch.empty_like(keys), torch.empty_like(vals)
             for pay in (0, 1):
+                m = n_kv if pay else n
+                k_m = keys if m == n else torch.cat([keys] * (m // n) + [keys[: m % n]])
+                vals = torch.arange(m, device="cuda", dtype=torch.int32)
+                out, vout = torch.empty_like(k_m), torch.empty_like(vals)
                 best = None
                 times = {}
                 for r in WIDTHS:
@@ -85,7 +88,7 @@ def tune_radix(ctx, n, reps, log):
                     _write_table(path, [(kb, pay, 64, r)], 0)
                     ctx.load_tuning(path)
                     v, vo = (vals, vout) if pay else (None, None)
-                    ms = _time(lambda: ctx.sort(keys, vals=v, out=out, vals_out=vo,
+                    ms = _time(lambda: ctx.sort(k_m, vals=v, out=out, vals_out=vo,
                                                 force=ahs.AHS_RADIX, key_type=kt, stream=stream),
                                reps, stream)
                     log(f"radix kb={kb} payload={pay} span_bits={span} r={r}: {ms:.4f} ms")
@@ -96,7 +99,8 @@ def tune_radix(ctx, n, reps, log):
                 if times[8] <= (1.0 + MARGIN) * best[1]:
                     best = (8, times[8])
                 rows.append((kb, pay, span, best[0]))
-            del keys, vals, out, vout
+                del k_m, vals, out, vout
+            del keys
             torch.cuda.empty_cache()
     ctx.load_tuning(None)
     return rows
@@ -128,7 +132,8 @@ def tune_batch_cutoff(ctx, n_seg, reps, log):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--n", type=int, default=1 << 25, help="keys per radix timing")
+    p.add_argument("--n", type=int, default=1 << 25, help="keys per keys-only radix timing")
+    p.add_argument("--n-kv", type=int, default=1 << 27, help="keys per key-value radix timing")
     p.add_argument("--reps", type=int, default=5)
     p.add_argument("--segments", type=int, default=5000, help="config-4 segments for the cutoff")
     p.add_argument("--out", default=DEFAULT_OUT)
@@ -144,13 +149,14 @@ def main(argv=None):
         lines.append(s)
 
     with ahs.Context(0, tuning_path=None) as ctx:
-        rows = tune_radix(ctx, args.n, args.reps, log)
+        rows = tune_radix(ctx, args.n, args.n_kv, args.reps, log)
         cutoff = tune_batch_cutoff(ctx, args.segments, args.reps, log)
     name = torch.cuda.get_device_name(0)
     with open(args.out, "w") as fh:
         fh.write("ahs-tuning 1\n")
         fh.write(f"# measured by paper_2506_20677_gb300/autotune.py on {name}: stable LSD radix on\n")
-        fh.write(f"# {args.n} uniform keys per range, median of {args.reps} CUDA-event timings per\n")
+        fh.write(f"# {args.n} uniform keys per range ({args.n_kv} with a payload), median of "
+                 f"{args.reps} CUDA-event timings per\n")
         fh.write("# candidate digit width; batched cutoff on the first "
                  f"{args.segments} segments of config 4.\n")
         for kb, pay, span, bits in rows:

@@ -550,3 +550,30 @@ extern "C" ahs_status ahs_sort_batch(ahs_ctx* ctx, const void* d_keys_in, void* 
     return ahs::run_batch(ctx, d_keys_in, d_keys_out, d_vals_in, d_vals_out, h_seg_offsets, n_seg,
                           ahs::key_desc(type), static_cast<cudaStream_t>(stream), info);
 }
+
+extern "C" ahs_status ahs_sort_batch_dev(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
+                                         const uint32_t* d_vals_in, uint32_t* d_vals_out,
+                                         const uint64_t* d_seg_offsets, uint32_t n_seg,
+                                         ahs_key_type type, void* stream, ahs_batch_info_t* info) {
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (!ctx || ctx->device < 0 || (n_seg && !d_seg_offsets)) return AHS_ERR_INVALID_ARG;
+    if (type < AHS_U32 || type > AHS_I64) return AHS_ERR_DTYPE;
+    if (n_seg == 0) return AHS_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return ahs::cuda_status(ctx, e);
+    // The offsets come to pinned host memory by kernel (behind the work
+    // already on the stream), then the host-planned batch runs as usual.
+    const size_t bytes = ((size_t)n_seg + 1) * sizeof(uint64_t);
+    ahs_status rc = ahs::ensure_stage(ctx, bytes);
+    if (rc != AHS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    e = ahs::launch_transfer(ctx->h_stage, d_seg_offsets, bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ahs::cuda_status(ctx, e);
+    // The staging buffer is reused by the batch itself: keep a copy.
+    std::vector<uint64_t> offs(static_cast<const uint64_t*>(ctx->h_stage),
+                               static_cast<const uint64_t*>(ctx->h_stage) + n_seg + 1);
+    return ahs_sort_batch(ctx, d_keys_in, d_keys_out, d_vals_in, d_vals_out, offs.data(), n_seg,
+                          type, stream, info);
+}
+

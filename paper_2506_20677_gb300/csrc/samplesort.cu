@@ -972,15 +972,19 @@ ahs_status radix_segs_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin
 // u = ord(x) - min (bin = u >> s, s = bitlen(span) - 16), so partition passes
 // whose bucket boundaries are bin boundaries know their bucket sizes without a
 // counting pass:
-//   Both strategies partition most significant digit first, by the bin:
-//   level 1 splits at boundaries of 256-bin blocks (the bin's high byte, by
-//   bit extraction) when no block holds more than twice its share of the
-//   keys, else at runs of consecutive bins of about n / 256 keys each (a
-//   digit of variable width, found by splitter search), so that a bin heavier
-//   than its share is a bucket of its own after one pass -- the common case
-//   of the low-entropy inputs the radix strategy is chosen for; level 2 cuts
-//   each run into buckets spanning at most 16 bits of u (one bin when the
-//   bins are 2^16 wide).  RADIX and GENERAL differ only in their trace names.
+//   RADIX (most significant digit first): pass 1 by the high byte of the bin,
+//     pass 2 by its low byte -- every bin's keys then sit at their final
+//     position, and a bin holds keys that differ only in their low s bits.
+//   GENERAL (sample sort with splitters from the histogram): level 1 splits at
+//     boundaries of 256-bin blocks when no block holds more than twice its
+//     share of the keys (classified by bit extraction), else at runs of bins
+//     of about n / 256 keys each (classified by a bin -> bucket table); level
+//     2 cuts each run into buckets spanning at most 16 bits of u.
+//   Level 1 writes the runs that level 2 does not split straight to the
+//   output.  (Measured on GB300 for Zipf keys: the table classifier is bound
+//   by the latency of its lookups -- the 64 KB table does not stay in the L1
+//   that shared memory leaves -- so a level 1 by runs costs more than the
+//   level-2 traffic it saves; the radix strategy keeps bit extraction.)
 // Buckets that fit a CTA are sorted in shared memory; larger ones (bins heavier
 // than a CTA, with no finer information in the histogram) are checked for a
 // single value and otherwise sample-sorted.  All lists of a sort are built on
@@ -1240,7 +1244,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     // Level 1: input -> temporary (runs that level 2 splits) or output.
     const unsigned long long share = std::max<unsigned long long>((n + 255) / 256, 1);
     bool blocks = nbins > 256;
-    for (uint32_t c = 0; blocks && c * 256 < nbins; ++c)
+    for (uint32_t c = 0; !msd && blocks && c * 256 < nbins; ++c)
         blocks = binpos[std::min(nbins, (c + 1) * 256)] - binpos[c * 256] <= 2 * share;
     std::vector<uint32_t> s1;
     if (blocks) {
@@ -1306,7 +1310,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     Pd.dshift = shift;
     Pd.src = Pr.src = ktmp;
     Pd.dst = Pr.dst = kout;
-    const uint32_t span_bins = shift >= 16 ? 1u : 1u << (16 - shift);
+    const uint32_t span_bins = msd || shift >= 16 ? 1u : 1u << (16 - shift);
     // Per level-1 run: -1 if it is final, else (pass, index) of its level-2 segment.
     std::vector<int32_t> split2(s1.size() + 1, -1);
     for (size_t g = 0; g <= s1.size(); ++g) {

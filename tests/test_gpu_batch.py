@@ -154,3 +154,20 @@ def test_config4_full(ahs, ctx, orc):
         if bad.numel():
             assert bool(torch.isin(bad, bounds).all()), "a segment is out of order"
     assert info.n_keys == total
+
+
+def test_batch_device_offsets_against_oracle(ahs, ctx, orc):
+    """ahs_sort_batch_dev: offsets resident on the device give the same result
+    as host offsets, segment by segment the oracle's sort (with a payload)."""
+    import torch
+    keys, offs = _mixed_segments(np.uint32, 5)
+    vals = np.arange(len(keys), dtype=np.uint32)
+    d_offs = torch.from_numpy(np.asarray(offs, dtype=np.uint64).view(np.int64)).cuda()
+    out, vout, info = ctx.sort_batch(dev(keys), d_offs, vals=dev(vals), key_type=ahs.AHS_U32)
+    ko, vo = host(out, np.uint32), host(vout, np.uint32)
+    for s in range(len(offs) - 1):
+        b, e = int(offs[s]), int(offs[s + 1])
+        ek, ev = orc.merge_sort(keys[b:e], vals[b:e])
+        assert np.array_equal(ko[b:e], ek), s
+        assert np.array_equal(vo[b:e], ev), s
+    assert info.n_seg == len(offs) - 1

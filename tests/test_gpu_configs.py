@@ -77,3 +77,19 @@ def test_config3_full(ahs, ctx):
     keys, vals = gdev.config3()
     r = ctx.sort(keys, vals=vals, force=ahs.AHS_RADIX, key_type=ahs.AHS_U64)
     check_stable_kv(host(keys, np.uint64), host(r.keys, np.uint64), host(r.vals, np.uint32))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", list("abcdef"))
+def test_config2_full_against_oracle(ahs, ctx, orc, variant):
+    """Config 2 at n = 2^28 in the launch configuration the bench times (AUTO
+    under the GB300 profile), element by element against the oracle's sort of
+    the host generator's keys (the oracle's counting sort for the k = 4096
+    array, its LSD radix sort for the others)."""
+    a = gen.config2(variant)
+    r = ctx.sort(dev(a), key_type=ahs.AHS_U32)
+    assert ahs.STRATEGY_NAMES[r.strategy] == EXPECT_GB300[variant]
+    out = host(r.keys, np.uint32)
+    del r
+    ko = orc.counting_sort(a) if variant == "a" else orc.radix_sort(a)
+    assert np.array_equal(out, ko)
