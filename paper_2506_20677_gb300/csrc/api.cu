@@ -428,6 +428,7 @@ void ahs_destroy(ahs_ctx* ctx) {
     if (ctx->aux) cudaFree(ctx->aux);
     if (ctx->side) cudaFree(ctx->side);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->h_coarse) cudaFreeHost(ctx->h_coarse);
     if (ctx->d_rec) cudaFree(ctx->d_rec);
     if (ctx->h_rec) cudaFreeHost(ctx->h_rec);
     delete ctx;

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "internal.h"
+#include "samplesort.h"
 #include "segsort.h"
 #include "trace.h"
 
@@ -50,7 +51,30 @@ struct HistSeg {
     unsigned long long begin;
     uint32_t size;
     uint32_t seg;
+    uint32_t slot;   // row of the coarse histogram (bin >> 8 counts), or kNoCoarse
+    uint32_t pad;
 };
+constexpr uint32_t kNoCoarse = 0xffffffffu;
+constexpr uint32_t kCoarse = 256;   // coarse buckets: the bin's high byte
+
+// Adds this CTA's counts of bins [lo, lo + len) (u32 counters, or u16 pairs
+// when PACKED) to the segment's coarse histogram row, one warp per bucket.
+template <bool PACKED>
+__device__ __forceinline__ void flush_coarse(const uint32_t* cnt, uint32_t lo, uint32_t len,
+                                             uint32_t* row) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t c0 = lo >> 8, c1 = (lo + len + 255) >> 8;
+    for (uint32_t c = c0 + warp; c < c1; c += kHistT / 32) {
+        uint32_t sum = 0;
+        for (uint32_t b = (c << 8) + lane; b < (c << 8) + 256; b += 32) {
+            if (b < lo || b >= lo + len) continue;
+            const uint32_t i = b - lo;
+            sum += PACKED ? (cnt[i >> 1] >> (16 * (i & 1))) & 0xffffu : cnt[i];
+        }
+        sum = warp_sum(sum);
+        if (lane == 0 && sum) atomicAdd(&row[c], sum);
+    }
+}
 
 __global__ void seg_init(SegFeat* f, uint32_t nseg) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,10 +189,11 @@ __device__ __forceinline__ double cc_sum(const uint32_t* cc, double inv, bool pe
 template <typename K>
 __global__ void __launch_bounds__(kHistT, 1)
 seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K flip,
-               SegFeat* __restrict__ feat) {
+               SegFeat* __restrict__ feat, uint32_t* __restrict__ coarse) {
     extern __shared__ __align__(16) uint32_t cnt[];
     __shared__ double red[kHistT / 32];
     __shared__ uint32_t cc[kCcMax];
+    __shared__ uint32_t cs[kCoarse];
     const HistSeg g = segs[blockIdx.x];
     const K mn = (K)feat[g.seg].min_ord;
     uint32_t s, nb;
@@ -178,7 +203,9 @@ seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
     double term = 0.0;
     const K* p = keys + g.begin;
     for (uint32_t i = threadIdx.x; i < kCcMax; i += kHistT) cc[i] = 0;
+    for (uint32_t i = threadIdx.x; i < kCoarse; i += kHistT) cs[i] = 0;
     const bool by_key = (uint64_t)g.size * 4 < nb;
+    const bool want_coarse = g.slot != kNoCoarse;
     if (by_key) {
         // Far fewer keys than bins: touch only the keys' own counters (zero
         // them, count), then every key adds one to cc[count of its bin]; a
@@ -197,7 +224,12 @@ seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
             const uint32_t c = (cnt[bin >> 1] >> (16 * (bin & 1))) & 0xffffu;
             if (c < kCcMax) atomicAdd(&cc[c], 1u);
             else term += plogp(c, inv) / (double)c;
+            if (want_coarse) atomicAdd(&cs[bin >> 8], 1u);
         });
+        __syncthreads();
+        if (want_coarse)
+            for (uint32_t i = threadIdx.x; i < kCoarse; i += kHistT)
+                if (cs[i]) coarse[(size_t)g.slot * kCoarse + i] = cs[i];
     } else {
         for (uint32_t i = threadIdx.x; i < words; i += kHistT) cnt[i] = 0;
         __syncthreads();
@@ -212,6 +244,7 @@ seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
             if (c0) { if (c0 < kCcMax) atomicAdd(&cc[c0], 1u); else term += plogp(c0, inv); }
             if (c1) { if (c1 < kCcMax) atomicAdd(&cc[c1], 1u); else term += plogp(c1, inv); }
         }
+        if (want_coarse) flush_coarse<true>(cnt, 0, nb, coarse + (size_t)g.slot * kCoarse);
     }
     __syncthreads();
     term += cc_sum(cc, inv, by_key);
@@ -224,7 +257,7 @@ seg_hist_small(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
 template <typename K>
 __global__ void __launch_bounds__(kHistT, 1)
 seg_hist_large(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K flip,
-               SegFeat* __restrict__ feat) {
+               SegFeat* __restrict__ feat, uint32_t* __restrict__ coarse) {
     extern __shared__ __align__(16) uint32_t cnt[];
     __shared__ double red[kHistT / 32];
     __shared__ uint32_t cc[kCcMax];
@@ -250,6 +283,7 @@ seg_hist_large(const K* __restrict__ keys, const HistSeg* __restrict__ segs, K f
         const uint32_t c = cnt[i];
         if (c) { if (c < kCcMax) atomicAdd(&cc[c], 1u); else term += plogp(c, inv); }
     }
+    if (g.slot != kNoCoarse) flush_coarse<false>(cnt, lo, len, coarse + (size_t)g.slot * kCoarse);
     __syncthreads();
     term += cc_sum(cc, inv, false);
     const double t = block_sum_1024(term, red);
@@ -337,25 +371,36 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
     const bool model = ctx->cfg.select_mode == AHS_SEL_MODEL;
     if (ctx->cfg.select_mode == AHS_SEL_CUSTOM) th = ctx->custom;
     else profile_thresholds(model ? AHS_SEL_GB300 : ctx->cfg.select_mode, &th);
+    // Keys-only segments the general class may take keep a coarse histogram
+    // (256 counts of the bin's high byte): its first partition level is then
+    // planned on the host with exact bucket sizes.
+    std::vector<uint32_t> slot_of(n_seg, kNoCoarse);
+    uint32_t n_slots = 0;
     for (uint32_t s = 0; s < n_seg; ++s) {
         const uint64_t b = offs[s] - base, n = offs[s + 1] - offs[s];
         for (uint64_t o = 0; o < n; o += kChunkKeys)
             chunks.push_back({b + o, (uint32_t)std::min<uint64_t>(kChunkKeys, n - o), s, b + n});
         // Entropy is only needed where the selector reads it.
         const bool need_h = n > th.n_t || model;
-        if (need_h && n > 1) (n <= kSmallHistMax ? hsmall : hlarge).push_back({b, (uint32_t)n, s});
+        if (need_h && n > 1) {
+            const uint32_t slot = (!payload && n > kBucketCap) ? n_slots++ : kNoCoarse;
+            slot_of[s] = slot;
+            (n <= kSmallHistMax ? hsmall : hlarge).push_back({b, (uint32_t)n, s, slot, 0});
+        }
     }
     const size_t b_feat = a256((size_t)n_seg * sizeof(SegFeat));
+    const size_t b_coarse = a256((size_t)n_slots * kCoarseBuckets * 4);
     const size_t b_chunks = a256(chunks.size() * sizeof(SegChunk));
     const size_t b_hs = a256(hsmall.size() * sizeof(HistSeg)), b_hl = a256(hlarge.size() * sizeof(HistSeg));
-    ahs_status rc = ensure_aux(ctx, b_feat + b_chunks + b_hs + b_hl);
+    ahs_status rc = ensure_aux(ctx, b_feat + b_coarse + b_chunks + b_hs + b_hl);
     if (rc == AHS_OK) rc = ensure_stage(ctx, std::max(b_chunks + b_hs + b_hl, b_feat));
     if (rc != AHS_OK) return rc;
     char* a = static_cast<char*>(ctx->aux);
     SegFeat* d_feat = reinterpret_cast<SegFeat*>(a);
-    SegChunk* d_chunks = reinterpret_cast<SegChunk*>(a + b_feat);
-    HistSeg* d_hs = reinterpret_cast<HistSeg*>(a + b_feat + b_chunks);
-    HistSeg* d_hl = reinterpret_cast<HistSeg*>(a + b_feat + b_chunks + b_hs);
+    uint32_t* d_coarse = reinterpret_cast<uint32_t*>(a + b_feat);
+    SegChunk* d_chunks = reinterpret_cast<SegChunk*>(a + b_feat + b_coarse);
+    HistSeg* d_hs = reinterpret_cast<HistSeg*>(a + b_feat + b_coarse + b_chunks);
+    HistSeg* d_hl = reinterpret_cast<HistSeg*>(a + b_feat + b_coarse + b_chunks + b_hs);
     char* hsb = static_cast<char*>(ctx->h_stage);
     std::memcpy(hsb, chunks.data(), chunks.size() * sizeof(SegChunk));
     std::memcpy(hsb + b_chunks, hsmall.data(), hsmall.size() * sizeof(HistSeg));
@@ -365,6 +410,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
     uint64_t keys_small = 0, keys_large = 0;
     for (const HistSeg& h : hsmall) keys_small += h.size;
     for (const HistSeg& h : hlarge) keys_large += h.size;
+    if (e == cudaSuccess && n_slots) e = launch_zero32(d_coarse, (uint64_t)n_slots * kCoarseBuckets, ctx->sms, st);
     if (e == cudaSuccess) {
         {
             TraceScope ts("batch_minmax", N, st);
@@ -377,7 +423,8 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
             e = cudaFuncSetAttribute(seg_hist_large<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSegHistSmem);
         if (e == cudaSuccess && !hsmall.empty()) {
             TraceScope ts("batch_hist_small", keys_small, st);
-            seg_hist_small<K><<<(uint32_t)hsmall.size(), kHistT, kSegHistSmem, st>>>(kin, d_hs, flip, d_feat);
+            seg_hist_small<K><<<(uint32_t)hsmall.size(), kHistT, kSegHistSmem, st>>>(kin, d_hs, flip, d_feat,
+                                                                                 d_coarse);
         }
         if (e == cudaSuccess && !hlarge.empty()) {
             TraceScope ts("batch_hist_large", keys_large, st);
@@ -393,17 +440,34 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            e = cudaLaunchKernelEx(&cfg, seg_hist_large<K>, kin, (const HistSeg*)d_hl, flip, d_feat);
+            e = cudaLaunchKernelEx(&cfg, seg_hist_large<K>, kin, (const HistSeg*)d_hl, flip, d_feat,
+                                   d_coarse);
         }
     }
+    // The records come back to the staging buffer, the coarse histograms to a
+    // pinned buffer of their own (read in place while the classes reuse the
+    // staging buffer).
+    const size_t coarse_bytes = (size_t)n_slots * kCoarseBuckets * 4;
+    if (coarse_bytes > ctx->h_coarse_bytes) {
+        if (ctx->h_coarse) cudaFreeHost(ctx->h_coarse);
+        ctx->h_coarse = nullptr;
+        ctx->h_coarse_bytes = 0;
+        if (e == cudaSuccess) e = cudaHostAlloc(&ctx->h_coarse, coarse_bytes + coarse_bytes / 2,
+                                                cudaHostAllocDefault);
+        if (e == cudaSuccess) ctx->h_coarse_bytes = coarse_bytes + coarse_bytes / 2;
+        else ctx->h_coarse = nullptr;
+    }
     if (e == cudaSuccess) e = launch_transfer(hsb, d_feat, (size_t)n_seg * sizeof(SegFeat), st);
+    if (e == cudaSuccess && n_slots) e = launch_transfer(ctx->h_coarse, d_coarse, coarse_bytes, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     const auto t1 = clock::now();
+    const uint32_t* coarse = static_cast<const uint32_t*>(ctx->h_coarse);
 
     // ---- 2. selection ------------------------------------------------------
     const SegFeat* hf = reinterpret_cast<const SegFeat*>(hsb);
     std::vector<SegRange> ident, small, radix, general, gsmall;
+    std::vector<HistRange> ghist;
     std::vector<CountSeg> counting;
     uint32_t radix_passes = 0;
     if (info) std::memset(info, 0, sizeof(*info));
@@ -451,6 +515,9 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
             break;
         default:
             if (n <= kBucketCap) gsmall.push_back(r);
+            else if (slot_of[s] != kNoCoarse)
+                ghist.push_back({r, f.hist_shift, f.descents < f.n / 4,
+                                 coarse + (size_t)slot_of[s] * kCoarseBuckets});
             else general.push_back(r);
             break;
         }
@@ -484,7 +551,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(ctx, e);
     }
-    if (!radix.empty() || !general.empty() || !gsmall.empty()) {
+    if (!radix.empty() || !general.empty() || !gsmall.empty() || !ghist.empty()) {
         rc = ensure_workspace(ctx, features_region(ctx->sms) + segsort_scratch_bytes(N, n_seg, kd.bytes, payload));
         if (rc != AHS_OK) return rc;
         void* scratch = static_cast<char*>(ctx->ws) + features_region(ctx->sms);
@@ -493,6 +560,13 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
             if (rc != AHS_OK) return rc;
             e = cudaStreamSynchronize(st);   // the radix lists in aux must be consumed first
             if (e != cudaSuccess) return cuda_status(ctx, e);
+        }
+        if (!ghist.empty()) {
+            // General segments with coarse histograms (and the small ones).
+            uint32_t lv = 0, nb = 0;
+            rc = run_batched_general_hist(ctx, kin, kout, N, ghist, gsmall, kd, scratch, st, &lv, &nb);
+            if (rc != AHS_OK) return rc;
+            gsmall.clear();
         }
         if (!general.empty() || !gsmall.empty()) {
             uint32_t lv = 0, nb = 0;

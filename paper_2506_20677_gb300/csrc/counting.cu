@@ -203,6 +203,29 @@ cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, c
     return cudaGetLastError();
 }
 
+// A list of copies (gather / scatter of many small arrays) in one launch: one
+// CTA per item at a time, 16-byte vectors where both ends allow them.
+__global__ void __launch_bounds__(256)
+copy_list(const CopyItem* __restrict__ items, uint32_t count) {
+    for (uint32_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const CopyItem c = items[it];
+        uint32_t* d = static_cast<uint32_t*>(c.dst);
+        const uint32_t* s = static_cast<const uint32_t*>(c.src);
+        const uintptr_t a = reinterpret_cast<uintptr_t>(d), b = reinterpret_cast<uintptr_t>(s);
+        if (((a ^ b) & 15u) == 0) {
+            const uint64_t head = head_elems<uint32_t>(s, c.words);
+            const uint64_t nvec = (c.words - head) / 4;
+            for (uint64_t i = threadIdx.x; i < head; i += 256) d[i] = s[i];
+            const uint4* sv = reinterpret_cast<const uint4*>(s + head);
+            uint4* dv = reinterpret_cast<uint4*>(d + head);
+            for (uint64_t i = threadIdx.x; i < nvec; i += 256) dv[i] = sv[i];
+            for (uint64_t i = head + nvec * 4 + threadIdx.x; i < c.words; i += 256) d[i] = s[i];
+        } else {
+            for (uint64_t i = threadIdx.x; i < c.words; i += 256) d[i] = s[i];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 transfer_words(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src,
                uint64_t words) {
@@ -235,6 +258,15 @@ cudaError_t launch_transfer(void* dst, const void* src, size_t bytes, cudaStream
         transfer_bytes<<<1, 256, 0, st>>>(static_cast<unsigned char*>(dst),
                                          static_cast<const unsigned char*>(src), bytes);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_list(const CopyItem* items, uint32_t count, uint64_t words, int sms,
+                             cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    TraceScope ts("copy_list", words, st);
+    const uint32_t grid = std::min<uint32_t>(count, 8u * (uint32_t)sms);
+    copy_list<<<grid, 256, 0, st>>>(items, count);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,9 @@ struct ahs_ctx {
     // Growable side buffer of the exact-entropy mode (its sorted copy).
     void* side = nullptr;
     size_t side_bytes = 0;
+    // Growable pinned host buffer of the batched form's coarse histograms.
+    void* h_coarse = nullptr;
+    size_t h_coarse_bytes = 0;
 
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::string last_cuda_error;

@@ -74,6 +74,18 @@ cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFea
 
 // Copy `words` 32-bit words (keys or payload) from src to dst.
 cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st);
+// Many copies of 32-bit words in one launch.  `items` must be readable by the
+// device (device memory, or pinned host memory, which the kernel reads in
+// place) until the launch completes; items of up to kCopyItemWords words
+// keep the CTAs balanced.
+struct CopyItem {
+    void* dst;
+    const void* src;
+    uint64_t words;
+};
+constexpr uint64_t kCopyItemWords = 1ull << 16;
+cudaError_t launch_copy_list(const CopyItem* items, uint32_t count, uint64_t words, int sms,
+                             cudaStream_t st);
 // Zero `words` 32-bit words.
 cudaError_t launch_zero32(void* dst, uint64_t words, int sms, cudaStream_t st);
 // Move `bytes` between pinned host memory (mapped into the device's address

@@ -59,6 +59,8 @@ struct SegDesc {
     uint32_t nchunks;
     uint32_t first_tile;   // index of the segment's first tile in the pass's tile order
     unsigned long long min_ord;
+    uint32_t dshift;       // digit passes: 0 = the pass's shift, else this segment's shift + 1
+    uint32_t pad;
 };
 struct TileDesc {
     unsigned long long begin;
@@ -71,7 +73,7 @@ struct ChunkDesc {
     uint32_t seg;
     uint32_t pad;
 };
-static_assert(sizeof(SegDesc) == 32 && sizeof(TileDesc) == 16 && sizeof(ChunkDesc) == 16, "layout");
+static_assert(sizeof(SegDesc) == 40 && sizeof(TileDesc) == 16 && sizeof(ChunkDesc) == 16, "layout");
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     // SplitMix64 output function (Steele, Lea & Flood 2014).
@@ -423,6 +425,10 @@ struct FastSmem {
     uint64_t bar[2];
 };
 
+static_assert(2 * (sizeof(FastSmem<uint32_t>) + 1024) <= 228 * 1024 &&
+                  2 * (sizeof(FastSmem<uint64_t>) + 1024) <= 228 * 1024,
+              "two partition CTAs per SM");
+
 // Tile k of a pass without a tile list: segment q owns tiles
 // [segs[q].first_tile, segs[q+1].first_tile), each of `tile_keys` keys but
 // its last.
@@ -505,7 +511,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             cls.m = nsplit[t.seg];
         } else {
             cls.mn = (K)sg.min_ord;
-            cls.shift = shift;
+            cls.shift = sg.dshift ? sg.dshift - 1 : shift;
         }
 
         // Bucket of each key and its slot in the tile's run of that bucket.
@@ -1397,6 +1403,137 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     return finish_large<K>(ctx, large, kout, n, flip, scratch, st, levels_out, buckets_out);
 }
 
+// The batched general class, keys only, with coarse histograms: see
+// run_batched_general_hist.  The pass's lists are planned and launched
+// first; the final buckets are listed while it runs.  Consecutive digit
+// buckets are merged into sort units of up to kUnitKeys keys (a small
+// segment would otherwise leave 256 buckets of a few keys each).
+constexpr uint32_t kUnitKeys = 4096;
+
+template <typename K>
+ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
+                          const std::vector<HistRange>& segs, const std::vector<SegRange>& extra,
+                          K flip, void* scratch, cudaStream_t st, uint32_t* levels_out,
+                          uint32_t* buckets_out) {
+    cudaError_t e = set_attrs<K, false>();
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    constexpr uint32_t TK = FastCfg<K>::kTileKeys;
+    constexpr uint32_t CS = cursor_stride<kDigit>();
+    // Two launches: segments whose warps often share a bucket (few descents)
+    // take the aggregated slot atomics.
+    size_t n_seg[2] = {0, 0}, n_til[2] = {0, 0};
+    for (const HistRange& h : segs) {
+        const int v = h.group ? 1 : 0;
+        ++n_seg[v];
+        n_til[v] += ceil_div(h.r.size, TK);
+    }
+    size_t b_seg[2], b_til[2], b_cur[2], at[2][3], total = 0;
+    for (int v = 0; v < 2; ++v) {
+        b_seg[v] = a256(n_seg[v] * sizeof(SegDesc));
+        b_til[v] = a256(n_til[v] * sizeof(TileDesc));
+        b_cur[v] = a256(n_seg[v] * CS * 4);
+        at[v][0] = total;
+        at[v][1] = total + b_seg[v];
+        at[v][2] = total + b_seg[v] + b_til[v];
+        total += b_seg[v] + b_til[v] + b_cur[v];
+    }
+    ahs_status rc = ensure_aux(ctx, total);
+    if (rc == AHS_OK) rc = ensure_stage(ctx, total);
+    if (rc != AHS_OK) return rc;
+    char* aux = static_cast<char*>(ctx->aux);
+    char* hs = static_cast<char*>(ctx->h_stage);
+    size_t q_seg[2] = {0, 0}, q_til[2] = {0, 0};
+    for (const HistRange& h : segs) {
+        const int v = h.group ? 1 : 0;
+        SegDesc d{};
+        d.begin = h.r.begin;
+        d.size = h.r.size;
+        d.min_ord = h.r.min_ord;
+        d.dshift = h.shift + 8 + 1;   // digit = bin >> 8 (a bin has <= 16 bits)
+        d.first_tile = (uint32_t)q_til[v];
+        const uint32_t q = (uint32_t)q_seg[v]++;
+        TileDesc* td = reinterpret_cast<TileDesc*>(hs + at[v][1]);
+        for (uint32_t o = 0; o < d.size; o += TK) td[q_til[v]++] = {d.begin + o, std::min(TK, d.size - o), q};
+        reinterpret_cast<SegDesc*>(hs + at[v][0])[q] = d;
+        // Cursors: each digit bucket's first position in the segment.
+        uint32_t* c = reinterpret_cast<uint32_t*>(hs + at[v][2]) + (size_t)q * CS;
+        uint32_t pos = 0;
+        for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
+            c[j] = pos;
+            pos += h.coarse[j];
+        }
+        if (pos != h.r.size) return AHS_ERR_CUDA;   // the histogram must describe the segment
+    }
+    e = launch_transfer(aux, hs, total, st);
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        if (!n_seg[v]) continue;
+        const uint32_t nt = (uint32_t)n_til[v];
+        const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
+        uint64_t keys = 0;
+        for (const HistRange& h : segs) keys += (h.group ? 1 : 0) == v ? h.r.size : 0;
+        TraceScope ts("batch_digit_scatter", keys, st);
+        const SegDesc* ds = reinterpret_cast<const SegDesc*>(aux + at[v][0]);
+        const TileDesc* dt = reinterpret_cast<const TileDesc*>(aux + at[v][1]);
+        uint32_t* dc = reinterpret_cast<uint32_t*>(aux + at[v][2]);
+        if (v)
+            ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                kin, kout, dt, ds, (uint32_t)n_seg[v], nt, nullptr, nullptr, flip, 0, dc, ctx->d_err);
+        else
+            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
+                kin, kout, dt, ds, (uint32_t)n_seg[v], nt, nullptr, nullptr, flip, 0, dc, ctx->d_err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    // While the pass runs: the sort units (runs of consecutive digit buckets
+    // of at most kUnitKeys keys; a single bucket up to a CTA's capacity) and
+    // the buckets heavier than a CTA.
+    FinalSet finals;
+    finals.reserve(extra.size() + n_total / (kUnitKeys / 2) + 64);
+    for (const SegRange& x : extra) finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
+    std::vector<SegRange> large;
+    for (const HistRange& h : segs) {
+        const uint32_t sh = h.shift + 8;
+        uint32_t pos = 0, j0 = 0, usz = 0;
+        auto close = [&](uint32_t j1) {   // unit = digit buckets [j0, j1)
+            if (usz >= 2) {
+                const unsigned long long lo =
+                    (unsigned long long)(K)(h.r.min_ord + ((unsigned long long)j0 << sh));
+                finals.add(final_bucket_bounded(h.r.begin + pos - usz, usz, 1, lo,
+                                                bitlen64((((unsigned long long)(j1 - j0)) << sh) - 1)));
+            }
+            j0 = j1;
+            usz = 0;
+        };
+        for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
+            const uint32_t sz = h.coarse[j];
+            if (sz > kBucketCap) {
+                close(j);
+                large.push_back({h.r.begin + pos, sz, 0ull});
+                pos += sz;
+                j0 = j + 1;
+                continue;
+            }
+            if (usz && usz + sz > kUnitKeys) close(j);
+            usz += sz;
+            pos += sz;
+        }
+        close(kCoarseBuckets);
+    }
+    // The pass's lists came from the staging buffer: wait before reusing it.
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    *levels_out = 1;
+    rc = finish_buckets(ctx, finals, scratch, kout, kin, nullptr, nullptr, nullptr,
+                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+    if (rc != AHS_OK || large.empty()) return rc;
+    uint32_t lv = 0, bk = 0;
+    rc = general_t<K, false>(ctx, kout, kout, nullptr, nullptr, n_total, large, {}, flip, scratch, st,
+                             &lv, &bk);
+    *levels_out += lv;
+    *buckets_out += bk;
+    return rc;
+}
+
 }  // namespace
 
 size_t samplesort_scratch_bytes(uint64_t n, uint32_t key_bytes, bool has_vals) {
@@ -1421,6 +1558,19 @@ ahs_status run_segmented_general(ahs_ctx* ctx, const void* kin, void* kout, cons
     }
     return v ? general_t<uint64_t, true>(ctx, (const uint64_t*)kin, (uint64_t*)kout, vin, vout, n_total, segs, extra, kd.flip, scratch, st, levels_out, buckets_out)
              : general_t<uint64_t, false>(ctx, (const uint64_t*)kin, (uint64_t*)kout, nullptr, nullptr, n_total, segs, extra, kd.flip, scratch, st, levels_out, buckets_out);
+}
+
+ahs_status run_batched_general_hist(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n_total,
+                                    const std::vector<HistRange>& segs,
+                                    const std::vector<SegRange>& extra, KeyDesc kd, void* scratch,
+                                    cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out) {
+    *levels_out = 0;
+    *buckets_out = 0;
+    if (kd.bytes == 4)
+        return batched_hist_t<uint32_t>(ctx, (const uint32_t*)kin, (uint32_t*)kout, n_total, segs, extra,
+                                        (uint32_t)kd.flip, scratch, st, levels_out, buckets_out);
+    return batched_hist_t<uint64_t>(ctx, (const uint64_t*)kin, (uint64_t*)kout, n_total, segs, extra,
+                                    kd.flip, scratch, st, levels_out, buckets_out);
 }
 
 ahs_status run_segmented_radix(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,

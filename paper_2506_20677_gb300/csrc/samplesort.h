@@ -14,6 +14,8 @@ namespace ahs {
 // two thirds full; the 4,608 class catches histogram bins of just over
 // 4,096 keys (2^28 keys in 2^16 bins).
 constexpr uint32_t kBucketCap = 8192;
+// Coarse histogram of a segment: counts of the feature histogram's bin >> 8.
+constexpr uint32_t kCoarseBuckets = 256;
 constexpr int kBucketClasses = 7;
 constexpr uint32_t kBucketClassCap[kBucketClasses] = {1024, 2048, 3072, 4096, 4608, 6144, 8192};
 

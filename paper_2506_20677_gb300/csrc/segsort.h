@@ -32,6 +32,26 @@ ahs_status run_segmented_general(ahs_ctx* ctx, const void* kin, void* kout, cons
                                  const std::vector<SegRange>& extra, KeyDesc kd, void* scratch,
                                  cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out);
 
+// A keys-only segment whose 256-bucket coarse histogram (counts of the
+// feature histogram's bin >> 8, bins of (ord(x) - min_ord) >> shift) is known.
+struct HistRange {
+    SegRange r;
+    uint32_t shift;              // the segment's histogram shift
+    bool group;                  // few descents: slot atomics aggregated per warp
+    const uint32_t* coarse;      // 256 counts (host memory)
+};
+
+// Keys only: one partition pass of every segment by the high byte of its
+// histogram bin, kin -> kout, with bucket offsets from the coarse histograms
+// (planned on the host before the launch, no counting pass), then the
+// shared-memory sorts of the buckets in place; buckets larger than a CTA
+// (heavy bins) are sorted in place by the sampled levels.  `extra` are
+// segments of at most one CTA's keys, sorted from kin in the same launches.
+ahs_status run_batched_general_hist(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n_total,
+                                    const std::vector<HistRange>& segs,
+                                    const std::vector<SegRange>& extra, KeyDesc kd, void* scratch,
+                                    cudaStream_t st, uint32_t* levels_out, uint32_t* buckets_out);
+
 // Stable LSD radix of every segment (digits of key - segment min, 8 bits a
 // pass, `passes` passes), kin -> kout, no host synchronisation.
 ahs_status run_segmented_radix(ahs_ctx* ctx, const void* kin, void* kout, const uint32_t* vin,

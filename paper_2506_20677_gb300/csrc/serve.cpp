@@ -165,6 +165,8 @@ struct ServeState {
     void* arena = nullptr;
     size_t arena_bytes = 0;
     LaneGen batch_gen, large_gen;
+    CopyItem* copy_items = nullptr;   // pinned gather / scatter lists of the batch lane
+    size_t copy_cap = 0;
     std::thread batch_thread, large_thread;
 
     // Move queued requests into the lanes while budget and slots allow (FIFO).
@@ -288,26 +290,47 @@ struct ServeState {
         char* out = in + kbytes;
         uint32_t* vin = pay ? reinterpret_cast<uint32_t*>(out + kbytes) : nullptr;
         uint32_t* vout = pay ? reinterpret_cast<uint32_t*>(out + kbytes + vbytes) : nullptr;
-        cudaError_t e = cudaSuccess;
-        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i) {
-            e = launch_copy32(in + offs[i] * kd.bytes, batch[i].keys_src(),
-                              batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
-            if (e == cudaSuccess && pay)
-                e = launch_copy32(vin + offs[i], batch[i].req.d_vals_in, batch[i].req.n,
-                                  batch_ctx->sms, batch_stream);
+        // Gather every request into the arena with one launch (items read
+        // in place from pinned host memory; the lane waits for the batch
+        // before it rewrites them).
+        std::vector<CopyItem> items;
+        auto add = [&](void* d, const void* src, uint64_t words) {
+            for (uint64_t o = 0; o < words; o += kCopyItemWords)
+                items.push_back({static_cast<uint32_t*>(d) + o, static_cast<const uint32_t*>(src) + o,
+                                 std::min(kCopyItemWords, words - o)});
+        };
+        for (size_t i = 0; i < batch.size(); ++i) {
+            add(in + offs[i] * kd.bytes, batch[i].keys_src(), batch[i].req.n * kd.bytes / 4);
+            if (pay) add(vin + offs[i], batch[i].req.d_vals_in, batch[i].req.n);
         }
+        const size_t n_gather = items.size();
+        for (size_t i = 0; i < batch.size(); ++i) {
+            add(batch[i].req.d_keys_out, out + offs[i] * kd.bytes, batch[i].req.n * kd.bytes / 4);
+            if (pay) add(batch[i].req.d_vals_out, vout + offs[i], batch[i].req.n);
+        }
+        cudaError_t e = cudaSuccess;
+        if (items.size() > copy_cap) {
+            if (copy_items) cudaFreeHost(copy_items);
+            copy_items = nullptr;
+            copy_cap = 0;
+            e = cudaHostAlloc(reinterpret_cast<void**>(&copy_items), items.size() * 2 * sizeof(CopyItem),
+                              cudaHostAllocDefault);
+            if (e != cudaSuccess) {
+                copy_items = nullptr;
+                return cuda_status(batch_ctx, e);
+            }
+            copy_cap = items.size() * 2;
+        }
+        std::memcpy(copy_items, items.data(), items.size() * sizeof(CopyItem));
+        e = launch_copy_list(copy_items, (uint32_t)n_gather, n * (kd.bytes / 4 + (pay ? 1 : 0)),
+                             batch_ctx->sms, batch_stream);
         if (e != cudaSuccess) return cuda_status(batch_ctx, e);
         ahs_batch_info_t info;
         ahs_status st = run_batch(batch_ctx, in, out, vin, vout, offs.data(),
                                   (uint32_t)batch.size(), kd, batch_stream, &info);
         if (st != AHS_OK) return st;
-        for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i) {
-            e = launch_copy32(batch[i].req.d_keys_out, out + offs[i] * kd.bytes,
-                              batch[i].req.n * kd.bytes / 4, batch_ctx->sms, batch_stream);
-            if (e == cudaSuccess && pay)
-                e = launch_copy32(batch[i].req.d_vals_out, vout + offs[i], batch[i].req.n,
-                                  batch_ctx->sms, batch_stream);
-        }
+        e = launch_copy_list(copy_items + n_gather, (uint32_t)(items.size() - n_gather),
+                             n * (kd.bytes / 4 + (pay ? 1 : 0)), batch_ctx->sms, batch_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(batch_stream);
         return cuda_status(batch_ctx, e);
     }
@@ -433,6 +456,7 @@ ahs_status ahs_serve_stop(ahs_ctx* ctx) {
     if (s->large_thread.joinable()) s->large_thread.join();
     cudaSetDevice(s->device);
     if (s->arena) cudaFree(s->arena);
+    if (s->copy_items) cudaFreeHost(s->copy_items);
     cudaStreamDestroy(s->batch_stream);
     cudaStreamDestroy(s->large_stream);
     ahs_destroy(s->batch_ctx);
