@@ -20,6 +20,10 @@ constexpr int kK1Threads = 512;
 template <typename K>
 struct K1Unroll { static constexpr int kU = 4; };
 constexpr int kK2Unroll = 4;
+// Up to this many bins K3 gives each bin a warp's lanes in eight warps that
+// split the slabs, instead of one thread per bin walking every slab: with few
+// bins that walk is a chain of L2 latencies on a handful of threads.
+constexpr uint32_t kK3DirectBins = 4096;
 constexpr uint32_t kU32Bins = kHistSmemBytes / 4;           // bins that fit as u32 counters
 
 template <typename K>
@@ -286,28 +290,52 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
     }
     const uint32_t nb = rec->nbins;
     const uint32_t nslabs = nb > kU32Bins ? k2_grid / 2 : k2_grid;   // see K2's two layouts
-    const uint32_t j = blockIdx.x * 256 + threadIdx.x;
-    double term = 0.0;
-    if (j < nb) {
-        unsigned long long tot = 0;
-        uint32_t c = 0;
-        for (; c + 4 <= nslabs; c += 4) {
-            const uint32_t a0 = slabs[(size_t)(c + 0) * kMaxBins + j];
-            const uint32_t a1 = slabs[(size_t)(c + 1) * kMaxBins + j];
-            const uint32_t a2 = slabs[(size_t)(c + 2) * kMaxBins + j];
-            const uint32_t a3 = slabs[(size_t)(c + 3) * kMaxBins + j];
-            tot += (unsigned long long)a0 + a1 + a2 + a3;
-        }
-        for (; c < nslabs; ++c) tot += slabs[(size_t)c * kMaxBins + j];
-        hist[j] = tot;
-        if (host_hist) host_hist[j] = tot;
-        if (tot) {
-            const double p = (double)tot / (double)n;
-            term = -p * log2(p);
-        }
-    }
     __shared__ double s_part[8];
     __shared__ bool s_last;
+    __shared__ unsigned long long s_acc[8][32];
+    double term = 0.0;
+    if (nb <= kK3DirectBins) {
+        // Few bins: block b takes bins [32 b, 32 b + 32) and its eight warps
+        // split the slabs between them, so every thread has a few loads in
+        // flight instead of one thread walking all ~150 slabs of a bin.
+        const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+        const uint32_t bin = blockIdx.x * 32 + lane;
+        unsigned long long acc = 0;
+        if (bin < nb)
+            for (uint32_t c = warp; c < nslabs; c += 8) acc += slabs[(size_t)c * kMaxBins + bin];
+        s_acc[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && bin < nb) {
+            unsigned long long tot = 0;
+            for (int w = 0; w < 8; ++w) tot += s_acc[w][lane];
+            hist[bin] = tot;
+            if (host_hist) host_hist[bin] = tot;
+            if (tot) {
+                const double p = (double)tot / (double)n;
+                term = -p * log2(p);
+            }
+        }
+    } else {
+        const uint32_t j = blockIdx.x * 256 + threadIdx.x;
+        if (j < nb) {
+            unsigned long long tot = 0;
+            uint32_t c = 0;
+            for (; c + 4 <= nslabs; c += 4) {
+                const uint32_t a0 = slabs[(size_t)(c + 0) * kMaxBins + j];
+                const uint32_t a1 = slabs[(size_t)(c + 1) * kMaxBins + j];
+                const uint32_t a2 = slabs[(size_t)(c + 2) * kMaxBins + j];
+                const uint32_t a3 = slabs[(size_t)(c + 3) * kMaxBins + j];
+                tot += (unsigned long long)a0 + a1 + a2 + a3;
+            }
+            for (; c < nslabs; ++c) tot += slabs[(size_t)c * kMaxBins + j];
+            hist[j] = tot;
+            if (host_hist) host_hist[j] = tot;
+            if (tot) {
+                const double p = (double)tot / (double)n;
+                term = -p * log2(p);
+            }
+        }
+    }
     term = warp_sum(term);
     if (lane_id() == 0) s_part[threadIdx.x >> 5] = term;
     __syncthreads();

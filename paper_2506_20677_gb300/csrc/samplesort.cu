@@ -1115,6 +1115,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
     if (e != cudaSuccess) return cuda_status(ctx, e);
     constexpr uint32_t TK = FastCfg<K>::kTileKeys;
     const uint32_t nbins = (uint32_t)hist.size();
+    const bool inplace = static_cast<const void*>(kin) == static_cast<const void*>(kout);
     std::vector<unsigned long long> binpos(nbins + 1, 0);
     for (uint32_t i = 0; i < nbins; ++i) binpos[i + 1] = binpos[i] + hist[i];
     if (binpos[nbins] != n) return AHS_ERR_CUDA;   // the histogram must describe these keys
@@ -1276,12 +1277,15 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         P1.src = kin;
         P1.dst = ktmp;
         // Runs that no later pass splits (at most a CTA's keys, or one bin)
-        // are written straight to the output.
-        P1.dst2 = kout;
-        P1.dsel.assign(cursor_stride<kDigit>(), 0);
-        for (size_t g = 0; g <= s1.size(); ++g) {
-            const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
-            P1.dsel[g] = !splits_further(b0, b1);
+        // are written straight to the output -- unless the output is the
+        // input, which other tiles of this pass are still reading.
+        if (!inplace) {
+            P1.dst2 = kout;
+            P1.dsel.assign(cursor_stride<kDigit>(), 0);
+            for (size_t g = 0; g <= s1.size(); ++g) {
+                const uint32_t b0 = g == 0 ? 0u : s1[g - 1], b1 = g == s1.size() ? nbins : s1[g];
+                P1.dsel[g] = !splits_further(b0, b1);
+            }
         }
         Blob A{stage, capA};
         const Placed pl = place(P1, A);
@@ -1359,9 +1363,13 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         const unsigned long long sz = binpos[b1] - binpos[b0];
         if (sz == 0) continue;
         if (split2[g] < 0) {
-            // Already in the output (level 1 wrote it there): sorted in place.
+            // Out of place, level 1 wrote the run to the output (sorted there
+            // in place); in place, it is in the temporary buffer.
+            const uint8_t where = inplace ? 0 : 1;
             if (sz <= kBucketCap && sz > 1)
-                cl.add(final_bucket_bounded(binpos[b0], (uint32_t)sz, 1, bin_lo(b0), range_bits(b0, b1)));
+                cl.add(final_bucket_bounded(binpos[b0], (uint32_t)sz, where, bin_lo(b0), range_bits(b0, b1)));
+            else if (inplace)
+                cl.add(final_bucket(binpos[b0], (uint32_t)sz, 0, false));   // copy out
             if (sz > kBucketCap) large.push_back({binpos[b0], (uint32_t)sz, 0ull});
             continue;
         }

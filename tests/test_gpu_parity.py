@@ -194,14 +194,19 @@ def test_identity_and_empty(ahs, ctx, orc):
     assert r.strategy == ahs.AHS_IDENTITY and r.keys.numel() == 0
 
 
-@pytest.mark.parametrize("force", ["RADIX", "GENERAL", "COUNTING"])
+@pytest.mark.parametrize("force", ["RADIX", "GENERAL", "COUNTING", "AUTO"])
 def test_in_place(ahs, ctx, orc, force):
+    """In place (output buffer = input buffer), keys only and with payload, on
+    inputs whose histogram-guided levels finish buckets after one pass (heavy
+    bins, clustered keys) as well as on uniform keys."""
     f = getattr(ahs, "AHS_" + force)
     for dt in (np.uint32, np.int64):
-        kind = "k4096" if force == "COUNTING" else "uniform_full"
-        for n in (100_003, 1 << 20):
-            _sort_case(ahs, ctx, orc, _gen(kind, n, dt, n), f, True, inplace=True)
-            _sort_case(ahs, ctx, orc, _gen(kind, n, dt, n + 1), f, False, inplace=True)
+        kinds = ["k4096"] if force == "COUNTING" else ["uniform_full", "zipf_wide", "clustered",
+                                                        "two_in_bin", "half_equal"]
+        for kind in kinds:
+            for n in (100_003, 1 << 20):
+                _sort_case(ahs, ctx, orc, _gen(kind, n, dt, n), f, True, inplace=True)
+                _sort_case(ahs, ctx, orc, _gen(kind, n, dt, n + 1), f, False, inplace=True)
 
 
 def test_misaligned_sort(ahs, ctx, orc):
