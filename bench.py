@@ -615,6 +615,14 @@ def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
         kt[name][1] += ms_
         kt[name][2] += items
     busy = sum(x[1] for x in kt.values())
+    # the largest host gaps between consecutive launches of the traced call
+    ev = sorted(tr, key=lambda e: e[3])
+    gaps = []
+    for a, b in zip(ev, ev[1:]):
+        g = b[3] - (a[3] + a[2])
+        if g > 0.2:
+            gaps.append((round(g, 3), a[0], b[0]))
+    gaps.sort(reverse=True)
     times_sorted = sorted(times)
     res = {"segments": n_seg, "keys": total, "batched_ms_p50": round(statistics.median(times), 3),
            "batched_ms_p99": round(times_sorted[min(len(times_sorted) - 1, int(0.99 * len(times_sorted)))], 3),
@@ -624,7 +632,8 @@ def run_batched(ctx, n_seg: int, steps: int, per_array: bool = True):
            "host_ms": {"features": round(info.ms_features, 3), "select": round(info.ms_select, 3),
                        "sort": round(info.ms_sort, 3)},
            "kernels": {k: {"launches": c, "ms": round(m, 3)} for k, (c, m, _) in
-                       sorted(kt.items(), key=lambda kv: -kv[1][1])}}
+                       sorted(kt.items(), key=lambda kv: -kv[1][1])},
+           "host_gaps_ms": gaps[:12]}
     if per_array:
         torch.cuda.synchronize()
         e0.record()

@@ -293,8 +293,13 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
     __shared__ double s_part[8];
     __shared__ bool s_last;
     __shared__ unsigned long long s_acc[8][32];
+    // Blocks past the bins have nothing to add: they leave at once, and the
+    // last of the active blocks reduces their partial sums.
+    const bool direct = nb <= kK3DirectBins;
+    const uint32_t active = direct ? (nb + 31) / 32 : (nb + 255) / 256;
+    if (blockIdx.x >= active) return;
     double term = 0.0;
-    if (nb <= kK3DirectBins) {
+    if (direct) {
         // Few bins: block b takes bins [32 b, 32 b + 32) and its eight warps
         // split the slabs between them, so every thread has a few loads in
         // flight instead of one thread walking all ~150 slabs of a bin.
@@ -344,12 +349,18 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
         for (int w = 0; w < 8; ++w) b += s_part[w];
         partials[blockIdx.x] = b;
         __threadfence();
-        s_last = (atomicAdd(&rec->k3_done, 1u) == gridDim.x - 1);
+        s_last = (atomicAdd(&rec->k3_done, 1u) == active - 1);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
+    // Last active block: the partial sums, one per thread, then the block.
+    double h = threadIdx.x < active ? __ldcg(partials + threadIdx.x) : 0.0;
+    h = warp_sum(h);
+    if (lane_id() == 0) s_part[threadIdx.x >> 5] = h;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double H = 0.0;
-    for (uint32_t b = 0; b < gridDim.x; ++b) H += __ldcg(partials + b);
+    for (int w = 0; w < 8; ++w) H += s_part[w];
     rec->entropy = H;
     rec->entropy_norm = nb > 1 ? H / log2((double)nb) : 0.0;
     rec->k3_done = 0;

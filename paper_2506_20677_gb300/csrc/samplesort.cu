@@ -516,39 +516,82 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
 
         // Bucket of each key and its slot in the tile's run of that bucket.
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
-        // A warp whose 32 keys share a bucket (runs of presorted input) takes
-        // its 32 slots with one atomic instead of 32 on the same counter.
+        // Each thread reads its keys as 16-byte vectors of V consecutive keys
+        // (key i is element i % V of the thread's vector i / V; the order of
+        // keys inside a tile is free without a payload).  A warp whose whole
+        // group of 32 V keys shares a bucket (runs of presorted input) takes
+        // its slots with one atomic; else a warp row of 32 keys that shares a
+        // bucket takes one; else one atomic per key.
         // GROUP (rows whose lanes often share buckets): every set of lanes
         // with one bucket takes its slots by one atomic of its lowest lane.
         // The match costs more the more distinct buckets a row holds, so the
         // host takes this variant only where lanes collide often.
+        constexpr int V = FastCfg<K>::kVec;
         const uint32_t lane = lane_id();
         K key[IPT];
         uint32_t br[IPT];
+        const bool vec_ok = sp.pad == 0;   // the tile starts on a 16-byte boundary
+#pragma unroll
+        for (int g = 0; g < IPT / V; ++g) {
+            const uint32_t p0 = (uint32_t)g * (kFastThreads * V) + tid * V;
+            if (vec_ok && p0 + V <= t.size) {
+                const Vec16<K> x = *reinterpret_cast<const Vec16<K>*>(&buf[p0]);
+#pragma unroll
+                for (int e = 0; e < V; ++e) key[g * V + e] = x.e[e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) key[g * V + e] = p0 + e < t.size ? buf[sp.pad + p0 + e] : K(0);
+            }
+        }
+        uint32_t bk[IPT];
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
-            const uint32_t p = i * kFastThreads + tid;
-            key[i] = p < t.size ? buf[sp.pad + p] : K(0);
-            const uint32_t b = p < t.size ? cls((K)(key[i] ^ flip)) : kCols;
-            const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
-            uint32_t r = 0;
-            if constexpr (GROUP) {
-                (void)b0;
-                const uint32_t m = __match_any_sync(AHS_FULL_MASK, b);
-                const uint32_t leader = __ffs(m) - 1;
-                uint32_t base = 0;
-                if (lane == leader && b < kCols) base = atomicAdd(&S.hist[b], (uint32_t)__popc(m));
-                r = __shfl_sync(AHS_FULL_MASK, base, leader) + __popc(m & lanemask_lt());
-            } else {
-                if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
+            const uint32_t p = (uint32_t)(i / V) * (kFastThreads * V) + tid * V + (uint32_t)(i % V);
+            bk[i] = p < t.size ? cls((K)(key[i] ^ flip)) : kCols;
+        }
+#pragma unroll
+        for (int g = 0; g < IPT / V; ++g) {
+            if constexpr (!GROUP) {
+                // The warp's whole group of 32 V consecutive keys in one bucket
+                // (runs of presorted input) takes its slots with one atomic.
+                const uint32_t b = bk[g * V];
+                bool lane_one = b < kCols;
+#pragma unroll
+                for (int e = 1; e < V; ++e) lane_one = lane_one && bk[g * V + e] == b;
+                const uint32_t bw = __shfl_sync(AHS_FULL_MASK, b, 0);
+                if (__all_sync(AHS_FULL_MASK, lane_one && b == bw)) {
                     uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
-                    r = __shfl_sync(AHS_FULL_MASK, base, 0) + lane;
-                } else {
-                    r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
+                    if (lane == 0) base = atomicAdd(&S.hist[b], 32u * V);
+                    base = __shfl_sync(AHS_FULL_MASK, base, 0) + V * lane;
+#pragma unroll
+                    for (int e = 0; e < V; ++e) br[g * V + e] = ((base + e) << 10) | b;
+                    continue;
                 }
             }
-            br[i] = (r << 10) | b;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const int i = g * V + e;
+                const uint32_t b = bk[i];
+                const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
+                uint32_t r = 0;
+                if constexpr (GROUP) {
+                    (void)b0;
+                    const uint32_t m = __match_any_sync(AHS_FULL_MASK, b);
+                    const uint32_t leader = __ffs(m) - 1;
+                    uint32_t base = 0;
+                    if (lane == leader && b < kCols) base = atomicAdd(&S.hist[b], (uint32_t)__popc(m));
+                    r = __shfl_sync(AHS_FULL_MASK, base, leader) + __popc(m & lanemask_lt());
+                } else {
+                    if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
+                        uint32_t base = 0;
+                        if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
+                        r = __shfl_sync(AHS_FULL_MASK, base, 0) + lane;
+                    } else {
+                        r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
+                    }
+                }
+                br[i] = (r << 10) | b;
+            }
         }
         __syncthreads();
 
@@ -587,6 +630,10 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         }
         __syncthreads();
 
+        // Write the staged tile: consecutive lanes write consecutive staged
+        // keys, so a warp's store covers one contiguous run.  (Four
+        // consecutive keys a thread, stored as vectors, measured slower on
+        // GB300: each store instruction then spans keys four apart.)
 #pragma unroll 4
         for (uint32_t j = tid; j < t.size; j += kFastThreads) {
             const K x = buf[j];

@@ -64,6 +64,23 @@ def test_noalloc_matches_features_on_consecutive_calls():
                 _same_as_oracle(f, orc)
 
 
+def test_noalloc_on_a_non_default_stream():
+    """The work runs on the caller's stream, after the work already queued there."""
+    import torch
+    import paper_2506_20677_gb300 as ahs
+    a = np.random.default_rng(7).integers(0, 2**32, size=(1 << 20) + 1, dtype=np.uint32)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        t = torch.from_numpy(a.view(np.int32)).to("cuda", non_blocking=False)
+        t2 = t.clone()                      # queued on st before the call
+    f = ahs.ahs_features_t()
+    for _ in range(2):
+        rc = ahs.lib.ahs_features_noalloc(ctypes.c_void_p(t2.data_ptr()), t2.numel(), ahs.AHS_U32,
+                                          ctypes.c_void_p(st.cuda_stream), ctypes.byref(f))
+        assert rc == ahs.AHS_OK
+        _same_as_oracle(f, oracle.features(a))
+
+
 def test_noalloc_edge_cases():
     import torch
     import paper_2506_20677_gb300 as ahs
