@@ -23,6 +23,7 @@
 #include "blocksort.cuh"
 #include "common.cuh"
 #include "ctx.h"
+#include "hostpar.h"
 #include "internal.h"
 #include "rank.cuh"
 #include "samplesort.h"
@@ -886,17 +887,28 @@ struct FinalSet {
 // Upload a final-bucket set to the auxiliary buffer and run the bucket sorts
 // (one launch per size class); synchronises before returning so the pinned
 // staging can be reused.
-ahs_status finish_buckets(ahs_ctx* ctx, const FinalSet& fs, const void* ktmp, const void* kout,
-                          const void* kin, const uint32_t* vtmp, uint32_t* vout, const uint32_t* vin,
-                          KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
+ahs_status finish_buckets_sets(ahs_ctx* ctx, const FinalSet* sets, size_t nsets, const void* ktmp,
+                               const void* kout, const void* kin, const uint32_t* vtmp, uint32_t* vout,
+                               const uint32_t* vin, KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
+    // Class k's list is the concatenation of every set's class-k entries.
     size_t nf = 0, at[kBucketClasses];
     uint32_t counts[kBucketClasses];
+    uint64_t keys[kBucketClasses];
+    uint32_t nsorted = 0;
     for (int k = 0; k < kBucketClasses; ++k) {
         at[k] = nf;
-        counts[k] = (uint32_t)fs.cls[k].size();
-        nf += counts[k];
+        size_t c = 0;
+        uint64_t kk = 0;
+        for (size_t i = 0; i < nsets; ++i) {
+            c += sets[i].cls[k].size();
+            kk += sets[i].keys[k];
+        }
+        counts[k] = (uint32_t)c;
+        keys[k] = kk;
+        nf += c;
     }
-    if (sorted) *sorted = fs.sorted;
+    for (size_t i = 0; i < nsets; ++i) nsorted += sets[i].sorted;
+    if (sorted) *sorted = nsorted;
     if (nf == 0) return AHS_OK;
     ahs_status rc = ensure_aux(ctx, nf * sizeof(FinalBucket));
     if (rc == AHS_OK) rc = ensure_stage(ctx, nf * sizeof(FinalBucket));
@@ -904,16 +916,38 @@ ahs_status finish_buckets(ahs_ctx* ctx, const FinalSet& fs, const void* ktmp, co
     FinalBucket* hf = static_cast<FinalBucket*>(ctx->h_stage);
     FinalBucket* df = static_cast<FinalBucket*>(ctx->aux);
     const FinalBucket* lists[kBucketClasses];
+    // (set, class) pieces copied into the pinned staging in parallel.
+    std::vector<std::pair<size_t, int>> piece;
+    std::vector<size_t> dst;
     for (int k = 0; k < kBucketClasses; ++k) {
-        std::memcpy(hf + at[k], fs.cls[k].data(), counts[k] * sizeof(FinalBucket));
+        size_t o = at[k];
+        for (size_t i = 0; i < nsets; ++i) {
+            if (!sets[i].cls[k].empty()) {
+                piece.push_back({i, k});
+                dst.push_back(o);
+            }
+            o += sets[i].cls[k].size();
+        }
         lists[k] = df + at[k];
     }
+    parallel_chunks(piece.size(), chunks_for(nf, 1u << 16), [&](size_t, size_t lo, size_t hi) {
+        for (size_t q = lo; q < hi; ++q) {
+            const std::vector<FinalBucket>& v = sets[piece[q].first].cls[piece[q].second];
+            std::memcpy(hf + dst[q], v.data(), v.size() * sizeof(FinalBucket));
+        }
+    });
     cudaError_t e = launch_transfer(df, hf, nf * sizeof(FinalBucket), st);
     if (e == cudaSuccess)
-        e = launch_bucket_finish(lists, counts, fs.keys, ktmp, kout, kin, const_cast<void*>(kout),
+        e = launch_bucket_finish(lists, counts, keys, ktmp, kout, kin, const_cast<void*>(kout),
                                  vtmp, vout, vin, vout, kd, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(ctx, e);
+}
+
+ahs_status finish_buckets(ahs_ctx* ctx, const FinalSet& fs, const void* ktmp, const void* kout,
+                          const void* kin, const uint32_t* vtmp, uint32_t* vout, const uint32_t* vin,
+                          KeyDesc kd, cudaStream_t st, uint32_t* sorted) {
+    return finish_buckets_sets(ctx, &fs, 1, ktmp, kout, kin, vtmp, vout, vin, kd, st, sorted);
 }
 
 // Partition levels by sampled splitters until every bucket fits a CTA, then
@@ -929,14 +963,15 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
     cudaError_t e = set_attrs<K, VALS>();
     if (e != cudaSuccess) return cuda_status(ctx, e);
 
-    FinalSet finals;
-    // Buckets hold a CTA's capacity / 2 keys on average: reserve for that.
-    finals.reserve(extra.size() + segs.size() + 2 * (n_total / (kBucketCap / 2)) + 64);
+    // Final buckets in several sets: one for the segments that need no
+    // level, then one per planning thread per level.
+    std::vector<FinalSet> finals(1);
+    finals[0].reserve(extra.size() + segs.size() + 64);
     for (const SegRange& x : extra)
-        finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
+        finals[0].add(final_bucket(x.begin, x.size, 2, x.size > 1));
     std::vector<SegRange> open;
     for (const SegRange& x : segs) {
-        if (x.size <= kBucketCap) finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
+        if (x.size <= kBucketCap) finals[0].add(final_bucket(x.begin, x.size, 2, x.size > 1));
         else open.push_back(x);
     }
     Level L;
@@ -966,28 +1001,41 @@ ahs_status general_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, u
         if (e != cudaSuccess) return cuda_status(ctx, e);
         const uint32_t* tot = reinterpret_cast<const uint32_t*>(hs);
         const uint32_t* base = reinterpret_cast<const uint32_t*>(hs + bread);
-        std::vector<SegRange> next;
-        for (uint32_t s = 0; s < ns; ++s) {
-            const uint32_t cols = 2 * split_count(L.segs[s].size) + 1;   // buckets in use
-            for (uint32_t j = 0; j < cols; ++j) {
-                const uint32_t sz = tot[(size_t)s * kCols + j];
-                if (sz == 0) continue;
-                const unsigned long long b0 = L.segs[s].begin + base[(size_t)s * kCols + j];
-                const bool equal = (j & 1u) != 0;
-                if (equal || sz == 1) {
-                    if (where == 0) finals.add(final_bucket(b0, sz, where, false));   // copy to output
-                } else if (sz <= kBucketCap) {
-                    finals.add(final_bucket(b0, sz, where, true));
-                } else {
-                    next.push_back({b0, sz, 0});
+        // Each segment's buckets: final (sorted or copied) or open at the
+        // next level -- planned by segment in parallel.
+        const size_t nch = chunks_for(ns, 256);
+        const size_t f0 = finals.size();
+        finals.resize(f0 + nch);
+        std::vector<std::vector<SegRange>> next_of(nch);
+        parallel_chunks(ns, nch, [&](size_t c, size_t lo, size_t hi) {
+            FinalSet& fs = finals[f0 + c];
+            uint64_t keys = 0;
+            for (size_t q = lo; q < hi; ++q) keys += L.segs[q].size;
+            fs.reserve(keys / (kBucketCap / 2) + 64);
+            for (size_t q = lo; q < hi; ++q) {
+                const uint32_t cols = 2 * split_count(L.segs[q].size) + 1;   // buckets in use
+                for (uint32_t j = 0; j < cols; ++j) {
+                    const uint32_t sz = tot[q * kCols + j];
+                    if (sz == 0) continue;
+                    const unsigned long long b0 = L.segs[q].begin + base[q * kCols + j];
+                    const bool equal = (j & 1u) != 0;
+                    if (equal || sz == 1) {
+                        if (where == 0) fs.add(final_bucket(b0, sz, where, false));   // copy to output
+                    } else if (sz <= kBucketCap) {
+                        fs.add(final_bucket(b0, sz, where, true));
+                    } else {
+                        next_of[c].push_back({b0, sz, 0});
+                    }
                 }
             }
-        }
+        });
+        std::vector<SegRange> next;
+        for (auto& v : next_of) next.insert(next.end(), v.begin(), v.end());
         open.swap(next);
     }
     *levels_out = level;
-    return finish_buckets(ctx, finals, ktmp, kout, kin, vtmp, vout, vin,
-                          KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+    return finish_buckets_sets(ctx, finals.data(), finals.size(), ktmp, kout, kin, vtmp, vout, vin,
+                               KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
 }
 
 template <typename K, bool VALS>
@@ -1497,28 +1545,47 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     if (rc != AHS_OK) return rc;
     char* aux = static_cast<char*>(ctx->aux);
     char* hs = static_cast<char*>(ctx->h_stage);
-    size_t q_seg[2] = {0, 0}, q_til[2] = {0, 0};
-    for (const HistRange& h : segs) {
-        const int v = h.group ? 1 : 0;
-        SegDesc d{};
-        d.begin = h.r.begin;
-        d.size = h.r.size;
-        d.min_ord = h.r.min_ord;
-        d.dshift = h.shift + 8 + 1;   // digit = bin >> 8 (a bin has <= 16 bits)
-        d.first_tile = (uint32_t)q_til[v];
-        const uint32_t q = (uint32_t)q_seg[v]++;
-        TileDesc* td = reinterpret_cast<TileDesc*>(hs + at[v][1]);
-        for (uint32_t o = 0; o < d.size; o += TK) td[q_til[v]++] = {d.begin + o, std::min(TK, d.size - o), q};
-        reinterpret_cast<SegDesc*>(hs + at[v][0])[q] = d;
-        // Cursors: each digit bucket's first position in the segment.
-        uint32_t* c = reinterpret_cast<uint32_t*>(hs + at[v][2]) + (size_t)q * CS;
-        uint32_t pos = 0;
-        for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
-            c[j] = pos;
-            pos += h.coarse[j];
+    // Each segment's launch, index and first tile (a running count), then
+    // the lists filled by segment in parallel.
+    const size_t ns = segs.size();
+    std::vector<uint32_t> q_of(ns), t_of(ns);
+    {
+        size_t q_seg[2] = {0, 0}, q_til[2] = {0, 0};
+        for (size_t i = 0; i < ns; ++i) {
+            const int v = segs[i].group ? 1 : 0;
+            q_of[i] = (uint32_t)q_seg[v]++;
+            t_of[i] = (uint32_t)q_til[v];
+            q_til[v] += ceil_div(segs[i].r.size, TK);
         }
-        if (pos != h.r.size) return AHS_ERR_CUDA;   // the histogram must describe the segment
     }
+    std::vector<uint8_t> bad(chunks_for(ns, 512), 0);
+    parallel_chunks(ns, bad.size(), [&](size_t c, size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+            const HistRange& h = segs[i];
+            const int v = h.group ? 1 : 0;
+            SegDesc d{};
+            d.begin = h.r.begin;
+            d.size = h.r.size;
+            d.min_ord = h.r.min_ord;
+            d.dshift = h.shift + 8 + 1;   // digit = bin >> 8 (a bin has <= 16 bits)
+            d.first_tile = t_of[i];
+            const uint32_t q = q_of[i];
+            TileDesc* td = reinterpret_cast<TileDesc*>(hs + at[v][1]) + t_of[i];
+            for (uint32_t o = 0, k = 0; o < d.size; o += TK, ++k)
+                td[k] = {d.begin + o, std::min(TK, d.size - o), q};
+            reinterpret_cast<SegDesc*>(hs + at[v][0])[q] = d;
+            // Cursors: each digit bucket's first position in the segment.
+            uint32_t* cur = reinterpret_cast<uint32_t*>(hs + at[v][2]) + (size_t)q * CS;
+            uint32_t pos = 0;
+            for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
+                cur[j] = pos;
+                pos += h.coarse[j];
+            }
+            if (pos != h.r.size) bad[c] = 1;   // the histogram must describe the segment
+        }
+    });
+    for (uint8_t b : bad)
+        if (b) return AHS_ERR_CUDA;
     e = launch_transfer(aux, hs, total, st);
     for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
         if (!n_seg[v]) continue;
@@ -1542,44 +1609,53 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     // While the pass runs: the sort units (runs of consecutive digit buckets
     // of at most kUnitKeys keys; a single bucket up to a CTA's capacity) and
     // the buckets heavier than a CTA.
-    FinalSet finals;
-    finals.reserve(extra.size() + n_total / (kUnitKeys / 2) + 64);
-    for (const SegRange& x : extra) finals.add(final_bucket(x.begin, x.size, 2, x.size > 1));
-    std::vector<SegRange> large;
-    for (const HistRange& h : segs) {
-        const uint32_t sh = h.shift + 8;
-        uint32_t pos = 0, j0 = 0, usz = 0;
-        auto close = [&](uint32_t j1) {   // unit = digit buckets [j0, j1)
-            if (usz >= 2) {
-                const unsigned long long lo =
-                    (unsigned long long)(K)(h.r.min_ord + ((unsigned long long)j0 << sh));
-                finals.add(final_bucket_bounded(h.r.begin + pos - usz, usz, 1, lo,
+    const size_t nch = chunks_for(ns, 512);
+    std::vector<FinalSet> finals(nch + 1);
+    std::vector<std::vector<SegRange>> large_of(nch);
+    for (const SegRange& x : extra) finals[nch].add(final_bucket(x.begin, x.size, 2, x.size > 1));
+    parallel_chunks(ns, nch, [&](size_t c, size_t lo, size_t hi) {
+        FinalSet& fs = finals[c];
+        uint64_t keys = 0;
+        for (size_t i = lo; i < hi; ++i) keys += segs[i].r.size;
+        fs.reserve(keys / (kUnitKeys / 2) + 64);
+        for (size_t i = lo; i < hi; ++i) {
+            const HistRange& h = segs[i];
+            const uint32_t sh = h.shift + 8;
+            uint32_t pos = 0, j0 = 0, usz = 0;
+            auto close = [&](uint32_t j1) {   // unit = digit buckets [j0, j1)
+                if (usz >= 2) {
+                    const unsigned long long lo_ord =
+                        (unsigned long long)(K)(h.r.min_ord + ((unsigned long long)j0 << sh));
+                    fs.add(final_bucket_bounded(h.r.begin + pos - usz, usz, 1, lo_ord,
                                                 bitlen64((((unsigned long long)(j1 - j0)) << sh) - 1)));
-            }
-            j0 = j1;
-            usz = 0;
-        };
-        for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
-            const uint32_t sz = h.coarse[j];
-            if (sz > kBucketCap) {
-                close(j);
-                large.push_back({h.r.begin + pos, sz, 0ull});
+                }
+                j0 = j1;
+                usz = 0;
+            };
+            for (uint32_t j = 0; j < kCoarseBuckets; ++j) {
+                const uint32_t sz = h.coarse[j];
+                if (sz > kBucketCap) {
+                    close(j);
+                    large_of[c].push_back({h.r.begin + pos, sz, 0ull});
+                    pos += sz;
+                    j0 = j + 1;
+                    continue;
+                }
+                if (usz && usz + sz > kUnitKeys) close(j);
+                usz += sz;
                 pos += sz;
-                j0 = j + 1;
-                continue;
             }
-            if (usz && usz + sz > kUnitKeys) close(j);
-            usz += sz;
-            pos += sz;
+            close(kCoarseBuckets);
         }
-        close(kCoarseBuckets);
-    }
+    });
+    std::vector<SegRange> large;
+    for (auto& v : large_of) large.insert(large.end(), v.begin(), v.end());
     // The pass's lists came from the staging buffer: wait before reusing it.
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     *levels_out = 1;
-    rc = finish_buckets(ctx, finals, scratch, kout, kin, nullptr, nullptr, nullptr,
-                        KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
+    rc = finish_buckets_sets(ctx, finals.data(), finals.size(), scratch, kout, kin, nullptr, nullptr,
+                             nullptr, KeyDesc{(uint32_t)sizeof(K), (uint64_t)flip}, st, buckets_out);
     if (rc != AHS_OK || large.empty()) return rc;
     uint32_t lv = 0, bk = 0;
     rc = general_t<K, false>(ctx, kout, kout, nullptr, nullptr, n_total, large, {}, flip, scratch, st,
