@@ -39,6 +39,7 @@ def algo_bytes_per_item(kernel: str, w: int, v: int) -> float:
         "bucket_sort_4.5k": 2 * (w + v), "bucket_sort_6k": 2 * (w + v), "bucket_sort_8k": 2 * (w + v),
         "blocksort_single": 2 * (w + v), "copy": 8,
         "msd_scatter": 2 * w, "msd_bin_minmax": w,
+        "sparse_count": w, "sparse_fill": w,
     }
     return table.get(kernel, 0.0)
 

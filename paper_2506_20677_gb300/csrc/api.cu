@@ -259,6 +259,15 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
             HistView hist;
             ahs_status rc = host_histogram(ctx, f, st, &hist);
             if (rc != AHS_OK) return rc;
+            if (sparse_radix_fits(n, kd.bytes, f.span, hist)) {
+                bool done = false;
+                rc = run_sparse_radix(ctx, kin, kout, n, kd, min_ord, st, &done, buckets);
+                if (rc != AHS_OK) return rc;
+                if (done) {
+                    *passes = 1;
+                    return AHS_OK;
+                }
+            }
             const size_t need = samplesort_scratch_bytes(n, kd.bytes, false);
             rc = ensure_workspace(ctx, freg + need);
             if (rc != AHS_OK) return rc;

@@ -516,7 +516,7 @@ ahs_status batch_t(ahs_ctx* ctx, const K* kin, K* kout, const uint32_t* vin, uin
         default:
             if (n <= kBucketCap) gsmall.push_back(r);
             else if (slot_of[s] != kNoCoarse)
-                ghist.push_back({r, f.hist_shift, f.descents < f.n / 4,
+                ghist.push_back({r, f.hist_shift, f.descents < f.n / 4, runs_likely(f.descents, f.n),
                                  coarse + (size_t)slot_of[s] * kCoarseBuckets});
             else general.push_back(r);
             break;

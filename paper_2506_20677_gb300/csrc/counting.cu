@@ -60,19 +60,29 @@ __device__ __forceinline__ uint32_t bin_from(const unsigned long long* __restric
     return bin_of(prefix, p, lo, hi);
 }
 
+// Dense (vals == nullptr): run j holds value mn + j.  Sparse: run j holds
+// value mn + vals[j], and the run count and a failure flag come from the
+// device (status[0] != 0: nothing to fill; status[1]: runs), so the fill can
+// be queued before the runs are known.
 template <typename K>
 __global__ void __launch_bounds__(kFillThreads)
 counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
-              const unsigned long long* __restrict__ prefix, uint32_t nb, K mn, K flip) {
+              const unsigned long long* __restrict__ prefix, uint32_t nb, K mn, K flip,
+              const K* __restrict__ vals = nullptr, const uint32_t* __restrict__ status = nullptr) {
     constexpr int V = Vec16<K>::kN;
     constexpr uint64_t kChunk = (uint64_t)kFillThreads * kFillUnroll;   // vectors
+    if (status) {
+        if (status[0] != 0) return;
+        nb = status[1];
+        if (nb == 0) return;
+    }
+    auto value = [&](uint32_t j) { return (K)(mn + (vals ? vals[j] : (K)j)) ^ flip; };
     if (blockIdx.x == 0) {
         const uint64_t tail0 = head + nvec * V;
-        if (threadIdx.x < head)
-            out[threadIdx.x] = (K)(mn + bin_of(prefix, threadIdx.x, 0, nb - 1)) ^ flip;
+        if (threadIdx.x < head) out[threadIdx.x] = value(bin_of(prefix, threadIdx.x, 0, nb - 1));
         if (threadIdx.x < n - tail0) {
             const uint64_t p = tail0 + threadIdx.x;
-            out[p] = (K)(mn + bin_of(prefix, p, 0, nb - 1)) ^ flip;
+            out[p] = value(bin_of(prefix, p, 0, nb - 1));
         }
     }
     // Each block fills a contiguous run of chunks.  Thread 0 finds the bins of
@@ -98,17 +108,25 @@ counting_fill(K* __restrict__ out, uint64_t n, uint64_t head, uint64_t nvec,
         const int slot = (int)((c - c0) & 1);
         const uint32_t lo = s_lo[slot], hi = s_hi[slot];
         if (threadIdx.x == 0 && c + 1 < c1) bins(c + 1, hi, slot ^ 1);
+        // A chunk inside one run (most chunks when runs are long) writes
+        // one value without searching.
+        const K one = value(lo);
 #pragma unroll
         for (int u = 0; u < kFillUnroll; ++u) {
             const uint64_t v = c * kChunk + (uint64_t)u * kFillThreads + threadIdx.x;
             if (v >= nvec) continue;
             const uint64_t p = head + v * V;
-            uint32_t j = bin_of(prefix, p, lo, hi);
             Vec16<K> r;
+            if (lo == hi) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                while (AHS_DCHECK(j < nb, "fill bin", j) && prefix[j + 1] <= p + e) ++j;
-                r.e[e] = (K)(mn + (K)j) ^ flip;
+                for (int e = 0; e < V; ++e) r.e[e] = one;
+            } else {
+                uint32_t j = bin_of(prefix, p, lo, hi);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    while (AHS_DCHECK(j < nb, "fill bin", j) && prefix[j + 1] <= p + e) ++j;
+                    r.e[e] = value(j);
+                }
             }
             if constexpr (sizeof(K) == 4) __stcs(reinterpret_cast<uint4*>(body + v * V), r.v);
             else __stcs(reinterpret_cast<ulonglong2*>(body + v * V), r.v);
@@ -169,7 +187,31 @@ cudaError_t fill_t(void* out_v, uint64_t n, K flip, const unsigned long long* hi
     return cudaGetLastError();
 }
 
+template <typename K>
+cudaError_t sparse_fill_t(void* out_v, uint64_t n, K flip, const unsigned long long* prefix,
+                          const K* vals, const uint32_t* status, K mn, int sms, cudaStream_t st) {
+    K* out = static_cast<K*>(out_v);
+    constexpr int V = Vec16<K>::kN;
+    const uint64_t head = head_elems<K>(out, n);
+    const uint64_t nvec = (n - head) / V;
+    const uint32_t g = grid_for(ceil_div(nvec, (uint64_t)kFillThreads * kFillUnroll), 1, sms, 8);
+    TraceScope ts("sparse_fill", n, st);
+    counting_fill<K><<<g, kFillThreads, 0, st>>>(out, n, head, nvec, prefix, 0u, mn, flip, vals, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_sparse_fill(void* out, uint64_t n, KeyDesc kd, const unsigned long long* prefix,
+                               const void* vals, const uint32_t* status, uint64_t min_ord, int sms,
+                               cudaStream_t st) {
+    if (kd.bytes == 4)
+        return sparse_fill_t<uint32_t>(out, n, (uint32_t)kd.flip, prefix,
+                                       static_cast<const uint32_t*>(vals), status, (uint32_t)min_ord,
+                                       sms, st);
+    return sparse_fill_t<uint64_t>(out, n, kd.flip, prefix, static_cast<const uint64_t*>(vals),
+                                   status, min_ord, sms, st);
+}
 
 cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFeatures*,
                                  const unsigned long long* hist, unsigned long long* prefix,

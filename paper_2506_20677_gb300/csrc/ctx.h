@@ -121,6 +121,19 @@ ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, 
                          uint32_t shift, uint32_t group, void* scratch, cudaStream_t st,
                          uint32_t* levels_out, uint32_t* buckets_out);
 
+// Keys-only radix sort of an input with few distinct values: the values are
+// counted in hash tables (one read of the keys), ranked, and the output is
+// filled run by run.  Tried when the histogram has at most kSparseMaxBins
+// non-empty bins (a lower bound on the distinct values) and n is at least
+// kSparseMinKeys; *done is false when the tables overflowed (more distinct
+// values than they hold), and the output is then untouched.  Synchronises
+// `st` once.
+constexpr uint64_t kSparseMinKeys = 1ull << 18;
+constexpr uint32_t kSparseMaxBins = 2048;
+bool sparse_radix_fits(uint64_t n, uint32_t key_bytes, uint64_t span, const HistView& hist);
+ahs_status run_sparse_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, KeyDesc kd,
+                            uint64_t min_ord, cudaStream_t st, bool* done, uint32_t* distinct);
+
 // Which partition levels aggregate the slot atomics of lanes that share a
 // bucket (measured on GB300: it pays where the lanes of a warp row often
 // share buckets without the whole row doing so, and costs up to 2.5x where
@@ -129,10 +142,18 @@ ahs_status run_msd_radix(ahs_ctx* ctx, const void* kin, void* kout, uint64_t n, 
 // path's one-atomic case).  The histogram adds a level when two random keys
 // of one bucket of the level before fall in the same bucket with probability
 // kGroupCollide or more (frequent keys).
+// kRunsLikely: neighbouring keys tend to share a bucket (few descents, or
+// few ascents: reversed runs), so the levels without aggregation check warp
+// rows for one shared bucket; without it (keys in random order: about n / 2
+// descents) those checks are skipped.
 constexpr uint32_t kGroupLevel1 = 1;
+constexpr uint32_t kRunsLikely = 2;
 constexpr double kGroupCollide = 0.25;
+inline bool runs_likely(unsigned long long descents, unsigned long long n) {
+    return descents < n / 4 || descents > n - n / 4;
+}
 inline uint32_t group_slots(const ahs_features_t& f) {
-    return f.descents < f.n / 4 ? kGroupLevel1 : 0u;
+    return (f.descents < f.n / 4 ? kGroupLevel1 : 0u) | (runs_likely(f.descents, f.n) ? kRunsLikely : 0u);
 }
 
 }  // namespace ahs

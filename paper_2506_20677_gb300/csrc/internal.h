@@ -72,6 +72,14 @@ cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFea
                                  const unsigned long long* hist, unsigned long long* prefix,
                                  uint64_t min_ord, uint32_t nbins, int sms, cudaStream_t st);
 
+// The same fill over a sparse set of values: run j (j < status[1]) holds
+// the value min + vals[j] at positions [prefix[j], prefix[j + 1]); nothing is
+// written when status[0] != 0.  The run count and flag are read on the
+// device, so the launch can be queued behind the kernels that produce them.
+cudaError_t launch_sparse_fill(void* out, uint64_t n, KeyDesc kd, const unsigned long long* prefix,
+                               const void* vals, const uint32_t* status, uint64_t min_ord, int sms,
+                               cudaStream_t st);
+
 // Copy `words` 32-bit words (keys or payload) from src to dst.
 cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st);
 // Many copies of 32-bit words in one launch.  `items` must be readable by the

@@ -446,11 +446,27 @@ __device__ __forceinline__ TileDesc tile_of(const SegDesc* segs, uint32_t nsegs,
     return {segs[lo].begin + off, size - off < tile_keys ? size - off : tile_keys, lo};
 }
 
+// How the slots of a tile's keys are taken (one shared atomic per key at
+// most):
+//  kSlotsPlain  one atomic per key (keys in random order);
+//  kSlotsRuns   a warp whose whole group of 32 V consecutive keys shares a
+//               bucket takes its slots with one atomic, else a warp row of
+//               32 keys that shares one, else one atomic per key (runs of
+//               presorted input; the checks cost about six instructions a
+//               key where no run ever forms);
+//  kSlotsGroup  every set of lanes with one bucket takes its slots by one
+//               atomic of its lowest lane (rows whose lanes often share
+//               buckets without the whole row doing so; the match costs more
+//               the more distinct buckets a row holds).
+constexpr int kSlotsPlain = 0;
+constexpr int kSlotsRuns = 1;
+constexpr int kSlotsGroup = 2;
+
 // dsel (nullable): one byte per (segment, bucket) cursor; a bucket whose byte
 // is set is written to dst2 instead of dst (at the same offsets), so that
 // buckets final after this pass can land in the output while the others go
 // to the temporary buffer of the next pass.
-template <typename K, int MODE, bool GROUP = false>
+template <typename K, int MODE, int SLOTS = kSlotsRuns>
 __global__ void __launch_bounds__(kFastThreads, 2)
 ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* __restrict__ tiles,
                 const SegDesc* __restrict__ segs, uint32_t nsegs, uint32_t ntiles,
@@ -515,18 +531,12 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             cls.shift = sg.dshift ? sg.dshift - 1 : shift;
         }
 
-        // Bucket of each key and its slot in the tile's run of that bucket.
+        // Bucket of each key and its slot in the tile's run of that bucket
+        // (SLOTS says how the slots are taken).
         // br = (slot << 10) | bucket; bucket kCols marks a lane past the tile.
         // Each thread reads its keys as 16-byte vectors of V consecutive keys
         // (key i is element i % V of the thread's vector i / V; the order of
-        // keys inside a tile is free without a payload).  A warp whose whole
-        // group of 32 V keys shares a bucket (runs of presorted input) takes
-        // its slots with one atomic; else a warp row of 32 keys that shares a
-        // bucket takes one; else one atomic per key.
-        // GROUP (rows whose lanes often share buckets): every set of lanes
-        // with one bucket takes its slots by one atomic of its lowest lane.
-        // The match costs more the more distinct buckets a row holds, so the
-        // host takes this variant only where lanes collide often.
+        // keys inside a tile is free without a payload).
         constexpr int V = FastCfg<K>::kVec;
         const uint32_t lane = lane_id();
         K key[IPT];
@@ -552,7 +562,7 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         }
 #pragma unroll
         for (int g = 0; g < IPT / V; ++g) {
-            if constexpr (!GROUP) {
+            if constexpr (SLOTS == kSlotsRuns) {
                 // The warp's whole group of 32 V consecutive keys in one bucket
                 // (runs of presorted input) takes its slots with one atomic.
                 const uint32_t b = bk[g * V];
@@ -573,16 +583,17 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
             for (int e = 0; e < V; ++e) {
                 const int i = g * V + e;
                 const uint32_t b = bk[i];
-                const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
                 uint32_t r = 0;
-                if constexpr (GROUP) {
-                    (void)b0;
+                if constexpr (SLOTS == kSlotsGroup) {
                     const uint32_t m = __match_any_sync(AHS_FULL_MASK, b);
                     const uint32_t leader = __ffs(m) - 1;
                     uint32_t base = 0;
                     if (lane == leader && b < kCols) base = atomicAdd(&S.hist[b], (uint32_t)__popc(m));
                     r = __shfl_sync(AHS_FULL_MASK, base, leader) + __popc(m & lanemask_lt());
+                } else if constexpr (SLOTS == kSlotsPlain) {
+                    r = b < kCols ? atomicAdd(&S.hist[b], 1u) : 0u;
                 } else {
+                    const uint32_t b0 = __shfl_sync(AHS_FULL_MASK, b, 0);
                     if (__all_sync(AHS_FULL_MASK, b == b0 && b < kCols)) {
                         uint32_t base = 0;
                         if (lane == 0) base = atomicAdd(&S.hist[b], 32u);
@@ -596,23 +607,19 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
         }
         __syncthreads();
 
-        // Reserve each bucket's run in the segment; tile-local run starts.
-        // A run that would leave its segment (a histogram that does not
-        // describe these keys) is reported and not written.
+        // Reserve each bucket's run in the segment (thread j, bucket j);
+        // tile-local run starts.  The reservation's result is first needed
+        // after the staging, so the atomic's round trip to L2 overlaps the
+        // scan and the staging stores.
+        const uint32_t j = tid;   // kFastThreads == kCols
+        uint32_t base;
         {
-            const uint32_t j = tid;   // kFastThreads == kCols
             const uint32_t c = S.hist[j];
             S.hist[j] = 0;
             // c == 0 for every column past the classifier's buckets.
-            const size_t cj = (size_t)t.seg * cursor_stride<MODE>() + j;
-            const uint32_t base = c ? atomicAdd(&cursor[cj], c) : 0u;
+            base = c ? atomicAdd(&cursor[(size_t)t.seg * cursor_stride<MODE>() + j], c) : 0u;
             uint32_t total;
-            const uint32_t ex = block_exclusive_scan<kFastThreads>(c, S.scan, &total);
-            S.tile_start[j] = ex;
-            K* d = (dsel != nullptr && c && dsel[cj]) ? dst2 : dst;
-            const bool inside = (unsigned long long)base + c <= sg.size;
-            if (!inside) report_error(err, kDevBadState);
-            S.gptr[j] = inside ? d + sg.begin + ((long long)base - (long long)ex) : nullptr;
+            S.tile_start[j] = block_exclusive_scan<kFastThreads>(c, S.scan, &total);
         }
         __syncthreads();
 
@@ -628,6 +635,20 @@ ss_scatter_keys(const K* __restrict__ src, K* __restrict__ dst, const TileDesc* 
                     if constexpr (MODE != kDigit) S.bid[lp] = (uint16_t)b;
                 }
             }
+        }
+        // Where bucket j's run goes.  A run that would leave its segment (a
+        // histogram that does not describe these keys) is reported and not
+        // written.  Only the reservation stays in a register across the
+        // staging; the run's start and size are read back.
+        {
+            const uint32_t ex = S.tile_start[j];
+            const uint32_t c = (j + 1 < kCols ? S.tile_start[j + 1] : t.size) - ex;
+            const SegDesc& sq = tiles ? segs[t.seg] : S.seg[t.seg];
+            const size_t cj = (size_t)t.seg * cursor_stride<MODE>() + j;
+            K* d = (dsel != nullptr && c && dsel[cj]) ? dst2 : dst;
+            const bool inside = (unsigned long long)base + c <= sq.size;
+            if (!inside) report_error(err, kDevBadState);
+            S.gptr[j] = inside ? d + sq.begin + ((long long)base - (long long)ex) : nullptr;
         }
         __syncthreads();
 
@@ -825,11 +846,25 @@ cudaError_t set_attrs() {
     if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kSplit>, sizeof(ScatterSmem<K, VALS>));
     if (e == cudaSuccess) e = set_smem(ss_scatter<K, VALS, kDigit>, sizeof(ScatterSmem<K, VALS>));
     if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kSplit>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, true>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable>, sizeof(FastSmem<K>));
-    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable, true>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, kSlotsPlain>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, kSlotsRuns>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kDigit, kSlotsGroup>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable, kSlotsPlain>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable, kSlotsRuns>, sizeof(FastSmem<K>));
+    if (e == cudaSuccess) e = set_smem(ss_scatter_keys<K, kTable, kSlotsGroup>, sizeof(FastSmem<K>));
     return e;
+}
+
+// ss_scatter_keys with its slot mode chosen at run time.
+template <typename K, int MODE, typename... A>
+cudaError_t launch_scatter_keys(int slots, uint32_t grid, size_t smem, cudaStream_t st, A... args) {
+    if (slots == kSlotsGroup)
+        ss_scatter_keys<K, MODE, kSlotsGroup><<<grid, kFastThreads, smem, st>>>(args...);
+    else if (slots == kSlotsPlain)
+        ss_scatter_keys<K, MODE, kSlotsPlain><<<grid, kFastThreads, smem, st>>>(args...);
+    else
+        ss_scatter_keys<K, MODE, kSlotsRuns><<<grid, kFastThreads, smem, st>>>(args...);
+    return cudaGetLastError();
 }
 
 // Final buckets written straight into the pinned staging, one region of
@@ -1241,7 +1276,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         std::vector<SegRange> segs;
         std::vector<std::vector<uint32_t>> starts;
         bool digit = false;
-        bool group = false;   // warp-aggregated slot atomics
+        int slots = kSlotsRuns;   // how the kernel takes the keys' slots
         uint32_t dshift = 0;
         const K* src = nullptr;
         K* dst = nullptr;
@@ -1318,23 +1353,16 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         const uint8_t* tbl = P.digit ? nullptr : reinterpret_cast<const uint8_t*>(w + pl.o_tbl);
         const uint32_t* tbn = P.digit ? nullptr : reinterpret_cast<const uint32_t*>(w + pl.o_tbn);
         const uint8_t* dsel = P.dsel.empty() ? nullptr : reinterpret_cast<const uint8_t*>(w + pl.o_dsel);
-        if (P.digit && P.group)
-            ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
-                ctx->d_err, P.dst2, dsel);
-        else if (P.digit)
-            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, nullptr, flip, P.dshift, d_cur,
-                ctx->d_err, P.dst2, dsel);
-        else if (P.group)
-            ss_scatter_keys<K, kTable, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, tbn, flip, shift, d_cur,
-                ctx->d_err, P.dst2, dsel, tbl);
-        else
-            ss_scatter_keys<K, kTable><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                P.src, P.dst, nullptr, d_segs, pl.ns, pl.nt, nullptr, tbn, flip, shift, d_cur,
-                ctx->d_err, P.dst2, dsel, tbl);
-        return cudaGetLastError();
+        const TileDesc* no_tiles = nullptr;
+        const K* no_splitters = nullptr;
+        if (P.digit)
+            return launch_scatter_keys<K, kDigit>(P.slots, grid, sizeof(FastSmem<K>), st, P.src, P.dst,
+                                                  no_tiles, d_segs, pl.ns, pl.nt, no_splitters,
+                                                  (const uint32_t*)nullptr, flip, P.dshift, d_cur,
+                                                  ctx->d_err, P.dst2, dsel, (const uint8_t*)nullptr);
+        return launch_scatter_keys<K, kTable>(P.slots, grid, sizeof(FastSmem<K>), st, P.src, P.dst,
+                                              no_tiles, d_segs, pl.ns, pl.nt, no_splitters, tbn, flip,
+                                              shift, d_cur, ctx->d_err, P.dst2, dsel, tbl);
     };
 
     // A level-1 run of bins [b0, b1) is split by level 2 when it holds more
@@ -1343,6 +1371,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
         return binpos[b1] - binpos[b0] > kBucketCap && b1 - b0 > 1;
     };
 
+    const int runs_slots = (group & kRunsLikely) ? kSlotsRuns : kSlotsPlain;
     // Level 1: input -> temporary (runs that level 2 splits) or output.
     const unsigned long long share = std::max<unsigned long long>((n + 255) / 256, 1);
     bool blocks = nbins > 256;
@@ -1368,7 +1397,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             const double share = (double)(binpos[b1] - binpos[b0]) / (double)n;
             d1 += share * share;
         }
-        P1.group = (group & kGroupLevel1) != 0 || d1 >= kGroupCollide;
+        P1.slots = (group & kGroupLevel1) != 0 || d1 >= kGroupCollide ? kSlotsGroup : runs_slots;
         P1.src = kin;
         P1.dst = ktmp;
         // Runs that no later pass splits (at most a CTA's keys, or one bin)
@@ -1410,7 +1439,7 @@ ahs_status keys_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n, K flip, 
             d2 += sq / (double)cg;
         }
         d2 /= (double)n;
-        Pd.group = Pr.group = d2 >= kGroupCollide;
+        Pd.slots = Pr.slots = d2 >= kGroupCollide ? kSlotsGroup : runs_slots;
     }
     Pd.dshift = shift;
     Pd.src = Pr.src = ktmp;
@@ -1522,16 +1551,20 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     if (e != cudaSuccess) return cuda_status(ctx, e);
     constexpr uint32_t TK = FastCfg<K>::kTileKeys;
     constexpr uint32_t CS = cursor_stride<kDigit>();
-    // Two launches: segments whose warps often share a bucket (few descents)
-    // take the aggregated slot atomics.
-    size_t n_seg[2] = {0, 0}, n_til[2] = {0, 0};
+    // One launch per slot mode: segments whose warps often share a bucket
+    // (few descents) take the aggregated slot atomics, reversed runs the
+    // run checks, keys in random order one atomic per key.
+    constexpr int kVariants = 3;
+    constexpr int kSlotsOf[kVariants] = {kSlotsPlain, kSlotsGroup, kSlotsRuns};
+    auto variant = [](const HistRange& h) { return h.group ? 1 : (h.runs ? 2 : 0); };
+    size_t n_seg[kVariants] = {0, 0, 0}, n_til[kVariants] = {0, 0, 0};
     for (const HistRange& h : segs) {
-        const int v = h.group ? 1 : 0;
+        const int v = variant(h);
         ++n_seg[v];
         n_til[v] += ceil_div(h.r.size, TK);
     }
-    size_t b_seg[2], b_til[2], b_cur[2], at[2][3], total = 0;
-    for (int v = 0; v < 2; ++v) {
+    size_t b_seg[kVariants], b_til[kVariants], b_cur[kVariants], at[kVariants][3], total = 0;
+    for (int v = 0; v < kVariants; ++v) {
         b_seg[v] = a256(n_seg[v] * sizeof(SegDesc));
         b_til[v] = a256(n_til[v] * sizeof(TileDesc));
         b_cur[v] = a256(n_seg[v] * CS * 4);
@@ -1550,9 +1583,9 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     const size_t ns = segs.size();
     std::vector<uint32_t> q_of(ns), t_of(ns);
     {
-        size_t q_seg[2] = {0, 0}, q_til[2] = {0, 0};
+        size_t q_seg[kVariants] = {0, 0, 0}, q_til[kVariants] = {0, 0, 0};
         for (size_t i = 0; i < ns; ++i) {
-            const int v = segs[i].group ? 1 : 0;
+            const int v = variant(segs[i]);
             q_of[i] = (uint32_t)q_seg[v]++;
             t_of[i] = (uint32_t)q_til[v];
             q_til[v] += ceil_div(segs[i].r.size, TK);
@@ -1562,7 +1595,7 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     parallel_chunks(ns, bad.size(), [&](size_t c, size_t lo, size_t hi) {
         for (size_t i = lo; i < hi; ++i) {
             const HistRange& h = segs[i];
-            const int v = h.group ? 1 : 0;
+            const int v = variant(h);
             SegDesc d{};
             d.begin = h.r.begin;
             d.size = h.r.size;
@@ -1587,23 +1620,19 @@ ahs_status batched_hist_t(ahs_ctx* ctx, const K* kin, K* kout, uint64_t n_total,
     for (uint8_t b : bad)
         if (b) return AHS_ERR_CUDA;
     e = launch_transfer(aux, hs, total, st);
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    for (int v = 0; v < kVariants && e == cudaSuccess; ++v) {
         if (!n_seg[v]) continue;
         const uint32_t nt = (uint32_t)n_til[v];
         const uint32_t grid = (uint32_t)std::min<uint64_t>(nt, 2ull * (uint64_t)ctx->sms);
         uint64_t keys = 0;
-        for (const HistRange& h : segs) keys += (h.group ? 1 : 0) == v ? h.r.size : 0;
+        for (const HistRange& h : segs) keys += variant(h) == v ? h.r.size : 0;
         TraceScope ts("batch_digit_scatter", keys, st);
         const SegDesc* ds = reinterpret_cast<const SegDesc*>(aux + at[v][0]);
         const TileDesc* dt = reinterpret_cast<const TileDesc*>(aux + at[v][1]);
         uint32_t* dc = reinterpret_cast<uint32_t*>(aux + at[v][2]);
-        if (v)
-            ss_scatter_keys<K, kDigit, true><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                kin, kout, dt, ds, (uint32_t)n_seg[v], nt, nullptr, nullptr, flip, 0, dc, ctx->d_err);
-        else
-            ss_scatter_keys<K, kDigit><<<grid, kFastThreads, sizeof(FastSmem<K>), st>>>(
-                kin, kout, dt, ds, (uint32_t)n_seg[v], nt, nullptr, nullptr, flip, 0, dc, ctx->d_err);
-        e = cudaGetLastError();
+        e = launch_scatter_keys<K, kDigit>(kSlotsOf[v], grid, sizeof(FastSmem<K>), st, kin, kout, dt, ds,
+                                           (uint32_t)n_seg[v], nt, nullptr, nullptr, flip, 0u, dc,
+                                           ctx->d_err);
     }
     if (e != cudaSuccess) return cuda_status(ctx, e);
     // While the pass runs: the sort units (runs of consecutive digit buckets

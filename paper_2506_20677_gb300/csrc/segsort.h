@@ -38,6 +38,7 @@ struct HistRange {
     SegRange r;
     uint32_t shift;              // the segment's histogram shift
     bool group;                  // few descents: slot atomics aggregated per warp
+    bool runs;                   // few descents or few ascents: warp rows checked for one bucket
     const uint32_t* coarse;      // 256 counts (host memory)
 };
 
