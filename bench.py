@@ -72,7 +72,7 @@ def measured_peaks():
 
 def kernel_source_hash(kernel: str):
     files = {"radix": "radix.cu", "sample": "samplesort.cu", "msd": "samplesort.cu",
-             "bucket": "blocksort.cuh",
+             "bucket": "blocksort.cuh", "sparse_count": "sparse.cu", "sparse_fill": "counting.cu",
              "features": "features.cu", "counting": "counting.cu", "copy": "counting.cu"}
     for pre, f in files.items():
         if kernel.startswith(pre):
