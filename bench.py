@@ -413,7 +413,7 @@ def run_ours(args, world, rank, local):
         # out); the timed region ends after ahs_wait_host.
         ctx.sort_host(host_in, host_out, key_type=ahs.AHS_U32, stream=stream, wait=False)
 
-    for _ in range(max(1, args.warmup // 2)):
+    for _ in range(max(2, args.warmup)):
         e2e_step()
     torch.cuda.synchronize()
     barrier(world)
