@@ -247,6 +247,11 @@ __device__ __forceinline__ void cp_async_key(K* smem_dst, const K* gmem_src) {
                  "l"(gmem_src), "n"(sizeof(K))
                  : "memory");
 }
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gmem_src)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Wait until at most one (the most recent) cp.async group is pending.

@@ -169,6 +169,7 @@ struct OnesweepSmem {
     uint32_t tile_id;
     K keys[TILE];
     uint32_t vals[VALS ? TILE : 1];
+    alignas(16) uint32_t vraw[VALS ? TILE : 1];   // the tile's payload in input order
 };
 
 template <typename K, bool VALS, int THREADS, int IPT, int MINB, int NB>
@@ -198,9 +199,21 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
     const uint32_t tile_base = tile * (uint32_t)TILE;
     const uint32_t wbase = tile_base + warp * WARP_ITEMS;
 
-    // Load warp-striped: item i of lane l is key wbase + 32 i + l.  (The
-    // payload is loaded when staged: loading it here with the keys measured
-    // slower on GB300, 1.51 against 1.25 ms per pass at 2^27 keys.)
+    // The tile's payload goes to shared memory by asynchronous copies that
+    // run while the keys are ranked (loading it into registers with the keys
+    // measured slower on GB300, 1.51 against 1.25 ms per pass at 2^27 keys:
+    // register pressure).
+    if constexpr (VALS) {
+        const uint32_t tile_n = (n - tile_base) < (uint32_t)TILE ? (n - tile_base) : (uint32_t)TILE;
+        const uint32_t* src = vals_in + tile_base;
+        const bool vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+        const uint32_t nv = vec ? tile_n / 4 : 0;
+        for (uint32_t q = tid; q < nv; q += THREADS) cp_async16(&S.vraw[4 * q], src + 4 * q);
+        for (uint32_t q = 4 * nv + tid; q < tile_n; q += THREADS) cp_async_key(&S.vraw[q], src + q);
+        cp_async_commit();
+    }
+
+    // Load warp-striped: item i of lane l is key wbase + 32 i + l.
     K key[IPT];
     uint32_t dig[IPT];
 #pragma unroll
@@ -243,6 +256,7 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
             if (tile != stall_tile) st_relaxed_gpu(&status[(size_t)tile * NB + q], flag | run);
         }
     }
+    if constexpr (VALS) cp_async_wait_all();   // this thread's payload copies; the barrier shows all
     __syncthreads();
     scan_digit_counts<THREADS, NB>(S.tile_count, S.tile_start, S.scan);
 
@@ -260,7 +274,7 @@ onesweep_pass(const K* __restrict__ keys_in, K* __restrict__ keys_out,
             if (dig[i] < (uint32_t)NB) {
                 const uint32_t lp = S.tile_start[dig[i]] + WC::get(S.warp_hist[warp], dig[i]) + rank[i];
                 if (AHS_DCHECK(lp < (uint32_t)TILE, "onesweep vstage", lp))
-                    S.vals[lp] = vals_in[wbase + 32 * i + lane];
+                    S.vals[lp] = S.vraw[warp * WARP_ITEMS + 32 * i + lane];
             }
         }
     }
