@@ -55,10 +55,15 @@ typedef enum {
 typedef enum { AHS_U32 = 0, AHS_U64 = 1, AHS_I32 = 2, AHS_I64 = 3 } ahs_key_type;
 
 /* Strategies of Section III-D..G.  IDENTITY copies (n < 2, k == 1, or an input
- * already in order under a profile that checks it). */
+ * already in order under a profile that checks it).  REVERSE returns an input
+ * found in reverse order reversed (§III-B's descending presorted edge case):
+ * only an AUTO sort picks it, under a profile that returns presorted inputs
+ * by a copy (GB300, MODEL, CUSTOM with sorted_identity), for an input with no
+ * ascent and at least one descent -- strictly decreasing when it carries a
+ * payload, so that the reversal is the stable order.  It cannot be forced. */
 typedef enum {
     AHS_AUTO = 0, AHS_IDENTITY = 1, AHS_SMALL = 2, AHS_COUNTING = 3,
-    AHS_RADIX = 4, AHS_GENERAL = 5
+    AHS_RADIX = 4, AHS_GENERAL = 5, AHS_REVERSE = 6
 } ahs_strategy;
 
 /* Selector profiles.
@@ -96,7 +101,8 @@ typedef enum {
  * (key - min) >> hist_shift, hist_shift = max(0, bitlen(span) - 16); for
  * k <= 65,536 the bins are the key values.  entropy_bits = -sum p log2 p over
  * non-empty bins (fp64), entropy_norm = entropy_bits / log2(nbins) (0 if
- * nbins == 1).  descents = #{i : key[i] > key[i+1]} (0: already in order).
+ * nbins == 1).  descents = #{i : key[i] > key[i+1]} (0: already in order),
+ * ascents = #{i : key[i] < key[i+1]} (0: in reverse order).
  * distinct = k', the number of distinct values, when known (ahs_entropy_exact
  * measures it; the feature pass leaves it 0 = unknown). */
 typedef struct {
@@ -110,6 +116,7 @@ typedef struct {
     double entropy_norm;
     uint64_t descents;
     uint64_t distinct;
+    uint64_t ascents;
 } ahs_features_t;
 
 /* FSM thresholds (Section III-A, Table II).  Comparisons follow the text:
@@ -143,9 +150,10 @@ typedef struct {
 typedef struct {
     ahs_strategy strategy;       /* the strategy that ran */
     int32_t features_valid;      /* 1 if features below were computed */
-    /* With AHS_AUTO under a profile that returns ordered inputs as they are
+    /* With AHS_AUTO under a profile that returns presorted inputs by a copy
      * (sorted_identity: GB300, MODEL, or CUSTOM thresholds that set it), an
-     * input found in order (descents == 0) gets no histogram pass: its
+     * input found in order (descents == 0) or in reverse order (ascents == 0;
+     * with a payload, descents == n - 1) gets no histogram pass: its
      * entropy_bits and entropy_norm are NaN. */
     ahs_features_t features;
     uint32_t passes;             /* radix digit passes run / sample-sort partition levels */
@@ -268,7 +276,10 @@ ahs_status ahs_entropy_exact(ahs_ctx* ctx, const void* d_keys, uint64_t n, ahs_k
 ahs_status ahs_select_fsm(const ahs_features_t* f, const ahs_thresholds_t* t,
                           ahs_strategy* out);
 /* Select with a profile (MODEL uses the ctx's loaded tree table; key_bytes and
- * has_payload are model inputs and are ignored by the FSM profiles). */
+ * has_payload are model inputs and are ignored by the FSM profiles).  Returns
+ * the profile's pick; ahs_sort with AHS_AUTO may differ from it by returning
+ * a reversed input by AHS_REVERSE and by running a COUNTING pick over more
+ * than 2^16 values on the radix path. */
 ahs_status ahs_select(const ahs_ctx* ctx, const ahs_features_t* f, ahs_select_mode mode,
                       uint32_t key_bytes, int32_t has_payload, ahs_strategy* out);
 

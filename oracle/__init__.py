@@ -18,8 +18,8 @@ _SRC = os.path.join(_HERE, "ahs_oracle.c")
 _LIB = os.path.join(_HERE, "libahs_oracle.so")
 
 U32, U64, I32, I64 = 0, 1, 2, 3
-AUTO, IDENTITY, SMALL, COUNTING, RADIX, GENERAL = range(6)
-STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL")
+AUTO, IDENTITY, SMALL, COUNTING, RADIX, GENERAL, REVERSE = range(7)
+STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL", "REVERSE")
 
 _DTYPE_TO_TYPE = {np.dtype(np.uint32): U32, np.dtype(np.uint64): U64,
                   np.dtype(np.int32): I32, np.dtype(np.int64): I64}
@@ -30,7 +30,7 @@ class Features(ctypes.Structure):
                 ("max_bits", ctypes.c_uint64), ("span", ctypes.c_uint64),
                 ("shift", ctypes.c_uint32), ("nbins", ctypes.c_uint32),
                 ("entropy", ctypes.c_double), ("entropy_norm", ctypes.c_double),
-                ("descents", ctypes.c_uint64)]
+                ("descents", ctypes.c_uint64), ("ascents", ctypes.c_uint64)]
 
 
 class Fsm(ctypes.Structure):

@@ -72,12 +72,16 @@ int orc_features(const void* keys, uint64_t n, int t, orc_features_t* f) {
     if (n == 0) { f->nbins = 0; return ORC_OK; }
 
     val_t mn = load_key(keys, 0, t), mx = mn;
-    uint64_t descents = 0;
+    uint64_t descents = 0, ascents = 0;
     for (uint64_t i = 0; i < n; ++i) {
         val_t x = load_key(keys, i, t);
         if (x < mn) mn = x;
         if (x > mx) mx = x;
-        if (i + 1 < n && x > load_key(keys, i + 1, t)) ++descents;
+        if (i + 1 < n) {
+            val_t y = load_key(keys, i + 1, t);
+            if (x > y) ++descents;
+            if (x < y) ++ascents;
+        }
     }
     uint64_t span = (uint64_t)(mx - mn);
     uint32_t bl = bitlen_u64(span);
@@ -106,6 +110,7 @@ int orc_features(const void* keys, uint64_t n, int t, orc_features_t* f) {
     f->entropy = H;
     f->entropy_norm = nbins > 1 ? H / log2((double)nbins) : 0.0;
     f->descents = descents;
+    f->ascents = ascents;
     return ORC_OK;
 }
 
@@ -545,7 +550,15 @@ int orc_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_o
     int s = force;
     if (s == ORC_AUTO) {
         if (!fsm) return ORC_EINVAL;
-        s = orc_select(&f, fsm);
+        /* The descending presorted edge case (Section III-B): under rules that
+         * return presorted inputs by a copy, an input with no ascent and at
+         * least one descent is returned reversed -- with a payload only when
+         * strictly decreasing, where the reversal is the stable order. */
+        if (fsm->sorted_identity && n >= 2 && f.descents > 0 && f.ascents == 0 &&
+            (!vals || f.descents == n - 1))
+            s = ORC_REVERSE;
+        else
+            s = orc_select(&f, fsm);
     }
     if (chosen) *chosen = s;
     size_t w = (t == ORC_U32 || t == ORC_I32) ? 4 : 8;
@@ -553,6 +566,12 @@ int orc_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* vals_o
     case ORC_IDENTITY:
         if (n) memmove(out, keys, n * w);
         if (vals && n) memmove(vals_out, vals, n * sizeof(uint32_t));
+        return ORC_OK;
+    case ORC_REVERSE:
+        for (uint64_t i = 0; i < n; ++i) {
+            memcpy((char*)out + (n - 1 - i) * w, (const char*)keys + i * w, w);
+            if (vals) vals_out[n - 1 - i] = vals[i];
+        }
         return ORC_OK;
     case ORC_SMALL:    return orc_insertion_sort(keys, out, vals, vals_out, n, t);
     case ORC_COUNTING: return orc_counting_sort(keys, out, vals, vals_out, n, t);

@@ -27,7 +27,7 @@ extern "C" {
 enum { ORC_U32 = 0, ORC_U64 = 1, ORC_I32 = 2, ORC_I64 = 3 };
 /* strategies (Section III-A: insertion / counting / radix / quick; plus identity) */
 enum { ORC_AUTO = 0, ORC_IDENTITY = 1, ORC_SMALL = 2, ORC_COUNTING = 3,
-       ORC_RADIX = 4, ORC_GENERAL = 5 };
+       ORC_RADIX = 4, ORC_GENERAL = 5, ORC_REVERSE = 6 };
 /* status */
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2, ORC_ERANGE = -3 };
 
@@ -42,6 +42,7 @@ typedef struct {
     double   entropy;    /* H = -sum_j p_j log2 p_j, p_j = c_j / n, over c_j > 0 */
     double   entropy_norm; /* h = H / log2(nbins), 0 when nbins == 1 */
     uint64_t descents;   /* number of i with key[i] > key[i+1] (0: already sorted) */
+    uint64_t ascents;    /* number of i with key[i] < key[i+1] (0: in reverse order) */
 } orc_features_t;
 
 /* Decision thresholds of the finite-state machine (Section III-A, Table II). */

@@ -23,10 +23,10 @@ AHS_OK, AHS_ERR_INVALID_ARG, AHS_ERR_DTYPE, AHS_ERR_OOM, AHS_ERR_BUDGET, AHS_ERR
     AHS_ERR_DEVICE_TIMEOUT, AHS_ERR_AGAIN, AHS_ERR_NOT_FOUND, AHS_ERR_UNIMPLEMENTED, \
     AHS_ERR_RANGE = range(11)
 AHS_U32, AHS_U64, AHS_I32, AHS_I64 = range(4)
-AHS_AUTO, AHS_IDENTITY, AHS_SMALL, AHS_COUNTING, AHS_RADIX, AHS_GENERAL = range(6)
+AHS_AUTO, AHS_IDENTITY, AHS_SMALL, AHS_COUNTING, AHS_RADIX, AHS_GENERAL, AHS_REVERSE = range(7)
 AHS_SEL_PAPER, AHS_SEL_LISTING6, AHS_SEL_GB300, AHS_SEL_MODEL, AHS_SEL_CUSTOM, AHS_SEL_LEMMA32 = range(6)
 AHS_DEBUG_STALL_ONE_TILE = 1
-STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL")
+STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL", "REVERSE")
 
 
 class ahs_features_t(ctypes.Structure):
@@ -34,7 +34,8 @@ class ahs_features_t(ctypes.Structure):
                 ("max_bits", ctypes.c_uint64), ("span", ctypes.c_uint64),
                 ("hist_shift", ctypes.c_uint32), ("nbins", ctypes.c_uint32),
                 ("entropy_bits", ctypes.c_double), ("entropy_norm", ctypes.c_double),
-                ("descents", ctypes.c_uint64), ("distinct", ctypes.c_uint64)]
+                ("descents", ctypes.c_uint64), ("distinct", ctypes.c_uint64),
+                ("ascents", ctypes.c_uint64)]
 
 
 class ahs_thresholds_t(ctypes.Structure):

@@ -78,10 +78,11 @@ void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out) {
     out->entropy_bits = r.entropy;
     out->entropy_norm = r.entropy_norm;
     out->descents = r.descents;
+    out->ascents = r.ascents;
 }
 
 ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
-                        cudaStream_t st, ahs_features_t* out, bool skip_sorted) {
+                        cudaStream_t st, ahs_features_t* out, uint32_t skip_sorted) {
     // Room for the counting sort's prefix too: that strategy reads the
     // histogram in place, and growing the workspace would not keep it.
     ahs_status rc = ensure_workspace(ctx, features_region(ctx->sms) + align256((kMaxBins + 1) * 8));
@@ -95,9 +96,13 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(ctx, e);
-    // The histogram kernel returned at once for an input found in order: its
+    // The histogram kernel returned at once for an input found presorted: its
     // trace entry processed no keys.
-    if (skip_sorted && ctx->h_rec->descents == 0)
+    const DevFeatures& r = *ctx->h_rec;
+    const bool skipped = ((skip_sorted & kSkipOrdered) && r.descents == 0) ||
+                         ((skip_sorted & kSkipReversed) && r.ascents == 0) ||
+                         ((skip_sorted & kSkipStrictReversed) && r.n >= 2 && r.descents == r.n - 1);
+    if (skipped)
         for (size_t i = mark; i < ctx->tracer.records.size(); ++i)
             if (std::strcmp(ctx->tracer.records[i].name, "features_histogram") == 0)
                 ctx->tracer.records[i].items = 0;
@@ -124,7 +129,13 @@ bool sorted_identity(const ahs_ctx* ctx) {
     }
 }
 
-ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload) {
+bool reversed_input(const ahs_features_t& f, bool payload) {
+    return f.n >= 2 && f.descents > 0 && f.ascents == 0 && (!payload || f.descents == f.n - 1);
+}
+
+ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload,
+                    bool allow_reverse) {
+    if (allow_reverse && reversed_input(f, payload)) return AHS_REVERSE;
     ahs_thresholds_t t;
     ahs_strategy s;
     switch (ctx->cfg.select_mode) {
@@ -229,6 +240,15 @@ ahs_status run_strategy(ahs_ctx* ctx, ahs_strategy s, const void* kin, void* kou
     case AHS_IDENTITY: {
         e = launch_copy32(kout, kin, n * kd.bytes / 4, ctx->sms, st);
         if (e == cudaSuccess && vin) e = launch_copy32(vout, vin, n, ctx->sms, st);
+        return cuda_status(ctx, e);
+    }
+    case AHS_REVERSE: {
+        // Only chosen for a reversed input (no ascents; strictly decreasing
+        // with a payload, so that the reversal keeps equal keys stable).
+        if (!reversed_input(f, vin != nullptr)) return AHS_ERR_INVALID_ARG;
+        e = launch_reverse(kout, kin, n, kd.bytes, ctx->sms, st);
+        if (e == cudaSuccess && vin) e = launch_reverse(vout, vin, n, 4, ctx->sms, st);
+        *passes = 1;
         return cuda_status(ctx, e);
     }
     case AHS_SMALL: {
@@ -576,14 +596,18 @@ ahs_status ahs_sort(ahs_ctx* ctx, const void* d_keys_in, void* d_keys_out,
 
     if (timing) cudaEventRecord(ctx->ev[0], st);
     ahs_features_t f;
-    // A profile that returns ordered inputs as they are needs no histogram
-    // for one: the feature pass skips it when K1 finds no descent.
-    ahs_status rc = run_features(ctx, d_keys_in, n, kd, st, &f,
-                                 force == AHS_AUTO && sorted_identity(ctx));
+    // A profile that returns presorted inputs by a copy (in order as they
+    // are, in reverse order reversed) needs no histogram for one: the feature
+    // pass skips it when K1 finds no descent, or no ascent (strictly
+    // decreasing keys with a payload).
+    const bool presorted = force == AHS_AUTO && sorted_identity(ctx);
+    const uint32_t skip = presorted ? (kSkipOrdered | (d_vals_in ? kSkipStrictReversed : kSkipReversed)) : 0u;
+    ahs_status rc = run_features(ctx, d_keys_in, n, kd, st, &f, skip);
     if (rc != AHS_OK) return rc;
     if (timing) cudaEventRecord(ctx->ev[1], st);
 
-    const ahs_strategy s = force == AHS_AUTO ? choose(ctx, f, kd.bytes, d_vals_in != nullptr) : force;
+    const ahs_strategy s =
+        force == AHS_AUTO ? choose(ctx, f, kd.bytes, d_vals_in != nullptr, presorted) : force;
     uint32_t passes = 0, buckets = 0;
     rc = run_strategy(ctx, s, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, kd, f, st, &passes,
                       &buckets);

@@ -157,6 +157,22 @@ copy32_scalar(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint
         dst[i] = src[i];
 }
 
+// out[n - 1 - i] = in[i].  Each thread swaps the pair (i, n - 1 - i), so
+// in == out is allowed; a warp's two reads and two writes each cover
+// consecutive addresses.
+template <typename T>
+__global__ void __launch_bounds__(256)
+reverse_pairs(T* out, const T* in, uint64_t n) {
+    const uint64_t half = (n + 1) / 2;
+    const uint64_t stride = (uint64_t)gridDim.x * 256;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < half; i += stride) {
+        const uint64_t j = n - 1 - i;
+        const T a = in[i], b = in[j];
+        out[i] = b;
+        out[j] = a;
+    }
+}
+
 __global__ void __launch_bounds__(256)
 zero32_vec(uint4* __restrict__ dst, uint64_t nvec) {
     const uint64_t stride = (uint64_t)gridDim.x * 256;
@@ -220,6 +236,20 @@ cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFea
         return fill_t<uint32_t>(out, n, (uint32_t)kd.flip, hist, prefix, (uint32_t)min_ord, nbins,
                                 sms, st);
     return fill_t<uint64_t>(out, n, kd.flip, hist, prefix, min_ord, nbins, sms, st);
+}
+
+cudaError_t launch_reverse(void* dst, const void* src, uint64_t n, uint32_t elem_bytes, int sms,
+                           cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    TraceScope ts("reverse", n, st);
+    const uint32_t g = grid_for((n + 1) / 2, 1024, sms, 8);
+    if (elem_bytes == 8)
+        reverse_pairs<unsigned long long><<<g, 256, 0, st>>>(static_cast<unsigned long long*>(dst),
+                                                             static_cast<const unsigned long long*>(src), n);
+    else
+        reverse_pairs<uint32_t><<<g, 256, 0, st>>>(static_cast<uint32_t*>(dst),
+                                                   static_cast<const uint32_t*>(src), n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st) {

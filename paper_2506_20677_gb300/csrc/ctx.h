@@ -66,12 +66,19 @@ namespace ahs {
 ahs_status ensure_workspace(ahs_ctx* ctx, size_t bytes);
 ahs_status cuda_status(ahs_ctx* ctx, cudaError_t e);
 // Features into ctx->h_rec (synchronises the stream); scratch at ctx->ws.
-// skip_sorted: an input found in order gets no histogram (entropy NaN); for
-// callers that then return it as it is.
+// skip_sorted (kSkip* flags): an input found presorted gets no histogram
+// (entropy NaN); for callers that then return it by a copy.
 ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd,
-                        cudaStream_t st, ahs_features_t* out, bool skip_sorted = false);
+                        cudaStream_t st, ahs_features_t* out, uint32_t skip_sorted = 0);
 void to_public(const DevFeatures& r, KeyDesc kd, ahs_features_t* out);
-ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload);
+// Reversed input: no ascents, at least one descent; with a payload strictly
+// decreasing (then reversing it is the stable sort).
+bool reversed_input(const ahs_features_t& f, bool payload);
+// The AUTO pick under the context's profile.  allow_reverse (single-array
+// sorts under a profile that returns presorted inputs by a copy): a reversed
+// input is returned reversed (AHS_REVERSE) before the profile's rules.
+ahs_strategy choose(const ahs_ctx* ctx, const ahs_features_t& f, uint32_t key_bytes, bool payload,
+                    bool allow_reverse = false);
 // Whether AUTO under the context's profile returns an input in order as it is.
 bool sorted_identity(const ahs_ctx* ctx);
 // Run one strategy on device-resident inputs whose features are in ctx->d_rec

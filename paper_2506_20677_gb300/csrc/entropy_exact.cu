@@ -163,7 +163,7 @@ extern "C" ahs_status ahs_entropy_exact(ahs_ctx* ctx, const void* d_keys, uint64
     ExactRec* rec = reinterpret_cast<ExactRec*>(static_cast<char*>(ctx->side) + a256(n * kd.bytes));
     // Sort the copy with the AUTO pipeline of the context's profile.
     ahs_features_t f;
-    ahs_status rc = run_features(ctx, d_keys, n, kd, st, &f, sorted_identity(ctx));
+    ahs_status rc = run_features(ctx, d_keys, n, kd, st, &f, sorted_identity(ctx) ? kSkipOrdered : 0u);
     if (rc != AHS_OK) return rc;
     uint32_t passes = 0, buckets = 0;
     rc = run_strategy(ctx, choose(ctx, f, kd.bytes, false), d_keys, sorted, nullptr, nullptr, n, kd,

@@ -28,11 +28,23 @@ constexpr uint32_t kU32Bins = kHistSmemBytes / 4;           // bins that fit as 
 
 template <typename K>
 __device__ __forceinline__ void k1_scalar(const K* keys, uint64_t i, uint64_t n, K flip, K& mn,
-                                          K& mx, unsigned long long& desc) {
+                                          K& mx, unsigned long long& desc, unsigned long long& asc) {
     const K o = keys[i] ^ flip;
     mn = o < mn ? o : mn;
     mx = o > mx ? o : mx;
-    if (i + 1 < n) desc += (o > (K)(keys[i + 1] ^ flip)) ? 1ull : 0ull;
+    if (i + 1 < n) {
+        const K on = (K)(keys[i + 1] ^ flip);
+        desc += (o > on) ? 1ull : 0ull;
+        asc += (o < on) ? 1ull : 0ull;
+    }
+}
+
+// An input K1 found presorted under the caller's skip flags: K2 and K3 have
+// nothing to do (block-uniform).
+__device__ __forceinline__ bool presorted_skip(const DevFeatures* rec, uint32_t flags) {
+    return ((flags & kSkipOrdered) && rec->descents == 0) ||
+           ((flags & kSkipReversed) && rec->ascents == 0) ||
+           ((flags & kSkipStrictReversed) && rec->n >= 2 && rec->descents == rec->n - 1);
 }
 
 template <typename K>
@@ -41,22 +53,22 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
                    unsigned long long* __restrict__ partials, DevFeatures* __restrict__ rec) {
     constexpr int V = Vec16<K>::kN;
     K mn = ~K(0), mx = 0;
-    unsigned long long desc = 0;
+    unsigned long long desc = 0, asc = 0;
     const uint32_t lane = lane_id();
     const uint64_t gtid = (uint64_t)blockIdx.x * kK1Threads + threadIdx.x;
     const uint64_t stride = (uint64_t)gridDim.x * kK1Threads;
 
     // Elements before the first 16-byte boundary, and after the last full vector.
     const uint64_t tail0 = head + nvec * V;
-    if (gtid < head) k1_scalar(keys, gtid, n, flip, mn, mx, desc);
-    if (gtid < n - tail0) k1_scalar(keys, tail0 + gtid, n, flip, mn, mx, desc);
+    if (gtid < head) k1_scalar(keys, gtid, n, flip, mn, mx, desc, asc);
+    if (gtid < n - tail0) k1_scalar(keys, tail0 + gtid, n, flip, mn, mx, desc, asc);
 
     // Vector body; lanes of a warp hold consecutive vectors, so the pair that
     // straddles two vectors is closed with a shuffle.  Lane 31 (and the owner
     // of the last vector) needs the next vector's first key from memory: it is
     // loaded together with the vectors so its latency overlaps theirs.
     const K* body = keys + head;
-    uint32_t dloc = 0;   // descents of this thread (fits 32 bits: < 2^32 keys per thread)
+    uint32_t dloc = 0, aloc = 0;   // descents, ascents of this thread (< 2^32 keys per thread)
     constexpr int kK1Unroll = K1Unroll<K>::kU;
     for (uint64_t wb = gtid - lane; wb < nvec; wb += stride * kK1Unroll) {
         Vec16<K> x[kK1Unroll];
@@ -84,35 +96,43 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
                     mx = o[j] > mx ? o[j] : mx;
                 }
 #pragma unroll
-                for (int j = 0; j + 1 < V; ++j) dloc += (o[j] > o[j + 1]) ? 1u : 0u;
+                for (int j = 0; j + 1 < V; ++j) {
+                    dloc += (o[j] > o[j + 1]) ? 1u : 0u;
+                    aloc += (o[j] < o[j + 1]) ? 1u : 0u;
+                }
                 if (head + (v + 1) * V < n) {
                     const K on = (lane < 31 && v + 1 < nvec) ? nxt : (K)(succ[u] ^ flip);
                     dloc += (o[V - 1] > on) ? 1u : 0u;
+                    aloc += (o[V - 1] < on) ? 1u : 0u;
                 }
             }
         }
     }
     desc += dloc;
+    asc += aloc;
 
     // Block reduction.
     __shared__ unsigned long long s_min[kK1Threads / 32], s_max[kK1Threads / 32],
-        s_desc[kK1Threads / 32];
+        s_desc[kK1Threads / 32], s_asc[kK1Threads / 32];
     __shared__ bool s_last;
     unsigned long long bmn = warp_min((unsigned long long)mn);
     unsigned long long bmx = warp_max((unsigned long long)mx);
     unsigned long long bd = warp_sum(desc);
+    unsigned long long ba = warp_sum(asc);
     const uint32_t warp = threadIdx.x >> 5;
-    if (lane == 0) { s_min[warp] = bmn; s_max[warp] = bmx; s_desc[warp] = bd; }
+    if (lane == 0) { s_min[warp] = bmn; s_max[warp] = bmx; s_desc[warp] = bd; s_asc[warp] = ba; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < kK1Threads / 32; ++w) {
             bmn = s_min[w] < bmn ? s_min[w] : bmn;
             bmx = s_max[w] > bmx ? s_max[w] : bmx;
             bd += s_desc[w];
+            ba += s_asc[w];
         }
-        partials[3 * blockIdx.x + 0] = bmn;
-        partials[3 * blockIdx.x + 1] = bmx;
-        partials[3 * blockIdx.x + 2] = bd;
+        partials[4 * blockIdx.x + 0] = bmn;
+        partials[4 * blockIdx.x + 1] = bmx;
+        partials[4 * blockIdx.x + 2] = bd;
+        partials[4 * blockIdx.x + 3] = ba;
         __threadfence();
         const uint32_t ticket = atomicAdd(&rec->k1_done, 1u);
         s_last = (ticket == gridDim.x - 1);
@@ -122,24 +142,27 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
 
     // Last block: combine all blocks and fix the binning (Section III-A reading:
     // s = max(0, bitlen(span) - 16), nbins = (span >> s) + 1).
-    unsigned long long gmn = ~0ull, gmx = 0, gd = 0;
+    unsigned long long gmn = ~0ull, gmx = 0, gd = 0, ga = 0;
     for (uint32_t b = threadIdx.x; b < gridDim.x; b += kK1Threads) {
-        const unsigned long long a = __ldcg(partials + 3 * b + 0);
-        const unsigned long long c = __ldcg(partials + 3 * b + 1);
+        const unsigned long long a = __ldcg(partials + 4 * b + 0);
+        const unsigned long long c = __ldcg(partials + 4 * b + 1);
         gmn = a < gmn ? a : gmn;
         gmx = c > gmx ? c : gmx;
-        gd += __ldcg(partials + 3 * b + 2);
+        gd += __ldcg(partials + 4 * b + 2);
+        ga += __ldcg(partials + 4 * b + 3);
     }
     gmn = warp_min(gmn);
     gmx = warp_max(gmx);
     gd = warp_sum(gd);
-    if (lane == 0) { s_min[warp] = gmn; s_max[warp] = gmx; s_desc[warp] = gd; }
+    ga = warp_sum(ga);
+    if (lane == 0) { s_min[warp] = gmn; s_max[warp] = gmx; s_desc[warp] = gd; s_asc[warp] = ga; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < kK1Threads / 32; ++w) {
             gmn = s_min[w] < gmn ? s_min[w] : gmn;
             gmx = s_max[w] > gmx ? s_max[w] : gmx;
             gd += s_desc[w];
+            ga += s_asc[w];
         }
         const unsigned long long span = gmx - gmn;
         const uint32_t bl = bitlen64(span);
@@ -147,6 +170,7 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
         rec->min_ord = gmn;
         rec->max_ord = gmx;
         rec->descents = gd;
+        rec->ascents = ga;
         rec->n = n;
         rec->span = span;
         rec->shift = s;
@@ -264,7 +288,7 @@ __global__ void __launch_bounds__(kHistThreads, 1)
 k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
              const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs, int skip_sorted) {
     extern __shared__ __align__(16) uint32_t sm32[];
-    if (skip_sorted && rec->descents == 0) return;   // block-uniform
+    if (presorted_skip(rec, (uint32_t)skip_sorted)) return;   // block-uniform
     const K mn = (K)rec->min_ord;
     const uint32_t s = rec->shift;
     const uint32_t nb = rec->nbins;
@@ -279,7 +303,7 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
            DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
            double* __restrict__ partials, DevFeatures* host_rec,
            unsigned long long* host_hist, int skip_sorted) {
-    if (skip_sorted && rec->descents == 0) {
+    if (presorted_skip(rec, (uint32_t)skip_sorted)) {
         // K2 counted nothing: no histogram, and the entropy is marked missing.
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             rec->entropy = __longlong_as_double(0x7ff8000000000000ll);

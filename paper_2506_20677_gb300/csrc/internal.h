@@ -10,10 +10,13 @@ namespace ahs {
 
 // Device-resident feature record, written by the feature kernels and copied to
 // the host in one piece.  Self-resetting block counters live here too.
+constexpr uint32_t kSkipOrdered = 1, kSkipReversed = 2, kSkipStrictReversed = 4;
+
 struct DevFeatures {
     unsigned long long min_ord;   // order-preserving image of the smallest key
     unsigned long long max_ord;
     unsigned long long descents;
+    unsigned long long ascents;
     unsigned long long n;
     unsigned long long span;
     uint32_t shift;
@@ -24,7 +27,7 @@ struct DevFeatures {
     uint32_t k3_done;
     uint32_t rh_done;             // radix digit-histogram kernel
     uint32_t pad0;
-    unsigned long long pad[6];
+    unsigned long long pad[5];
 };
 static_assert(sizeof(DevFeatures) == 128, "DevFeatures layout");
 
@@ -57,8 +60,10 @@ struct FeatureScratch {
     // Optional pinned host mirrors that K3 fills (null: device copies only).
     DevFeatures* host_rec = nullptr;
     unsigned long long* host_hist = nullptr;   // nbins counts
-    // K2 and K3 skip an input K1 found in order (no histogram; entropy NaN).
-    bool skip_sorted = false;
+    // K2 and K3 skip an input K1 found presorted (no histogram; entropy NaN):
+    // kSkipOrdered: no descents; kSkipReversed: no ascents (keys only);
+    // kSkipStrictReversed: strictly decreasing (with a payload).
+    uint32_t skip_sorted = 0;
 };
 uint32_t k1_blocks(uint64_t n, int sms);
 size_t features_scratch_bytes(int sms);
@@ -79,6 +84,10 @@ cudaError_t launch_counting_fill(void* out, uint64_t n, KeyDesc kd, const DevFea
 cudaError_t launch_sparse_fill(void* out, uint64_t n, KeyDesc kd, const unsigned long long* prefix,
                                const void* vals, const uint32_t* status, uint64_t min_ord, int sms,
                                cudaStream_t st);
+
+// dst[n - 1 - i] = src[i] for elements of 4 or 8 bytes; dst == src allowed.
+cudaError_t launch_reverse(void* dst, const void* src, uint64_t n, uint32_t elem_bytes, int sms,
+                           cudaStream_t st);
 
 // Copy `words` 32-bit words (keys or payload) from src to dst.
 cudaError_t launch_copy32(void* dst, const void* src, uint64_t words, int sms, cudaStream_t st);

@@ -117,5 +117,6 @@ extern "C" ahs_status ahs_features_noalloc(const void* d_keys, uint64_t n, ahs_k
     h_out->entropy_bits = r.entropy;
     h_out->entropy_norm = r.entropy_norm;
     h_out->descents = r.descents;
+    h_out->ascents = r.ascents;
     return AHS_OK;
 }

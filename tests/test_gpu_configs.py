@@ -28,7 +28,7 @@ def ctx(ahs):
 
 
 EXPECT_GB300 = {"a": "COUNTING", "b": "RADIX", "c": "GENERAL", "d": "IDENTITY", "e": "GENERAL",
-                "f": "GENERAL"}
+                "f": "REVERSE"}
 NAMED = {"a": "COUNTING", "b": "RADIX", "c": "GENERAL", "d": "GENERAL", "e": "GENERAL",
          "f": "GENERAL"}
 

@@ -25,7 +25,10 @@ MUTATIONS = {
     "bin_width_15": [("bl > 16 ? bl - 16 : 0", "bl > 15 ? bl - 15 : 0")],
     "bins_without_min": [("uint64_t u = (uint64_t)(load_key(keys, i, t) - mn);",
                           "uint64_t u = (uint64_t)(load_key(keys, i, t));")],
-    "descent_non_strict": [("x > load_key(keys, i + 1, t)", "x >= load_key(keys, i + 1, t)")],
+    "descent_non_strict": [("if (x > y) ++descents;", "if (x >= y) ++descents;")],
+    "ascent_non_strict": [("if (x < y) ++ascents;", "if (x <= y) ++ascents;")],
+    "reverse_ignores_tied_payload": [("(!vals || f.descents == n - 1))", "1)")],
+    "reverse_under_every_profile": [("if (fsm->sorted_identity && n >= 2", "if (n >= 2")],
     "insertion_unstable": [("a[j - 1] > key", "a[j - 1] >= key")],
     "counting_reverse_placement": [("for (uint64_t i = 0; i < n; ++i) {       /* input order",
                                     "for (uint64_t i = n; i-- > 0;) {       /* input order")],
@@ -70,6 +73,28 @@ def _pins_pass() -> bool:
                 return False
             if f.descents != int(np.count_nonzero(keys[:-1] > keys[1:])):
                 return False
+            if f.ascents != int(np.count_nonzero(keys[:-1] < keys[1:])):
+                return False
+        # Reversed inputs (Section III-B's descending presorted case) under
+        # rules that return presorted inputs by a copy: keys only with ties,
+        # a payload only when strictly decreasing; never under PAPER.
+        rng = np.random.default_rng(1)
+        gb = oracle.Profile(4096, 65536, 10**6, sorted_identity=True)
+        tied = np.sort(rng.integers(0, 50, size=300).astype(np.uint32))[::-1].copy()
+        strict = np.sort(rng.choice(10**6, size=300, replace=False).astype(np.uint32))[::-1].copy()
+        v = np.arange(300, dtype=np.uint32)
+        k, _, ch, f = oracle.sort(tied, profile=gb)
+        if ch != oracle.REVERSE or f.ascents != 0 or not np.array_equal(k, np.sort(tied)):
+            return False
+        k, vo, ch, _ = oracle.sort(tied, v, profile=gb)
+        exp_v = np.array(sorted(range(300), key=lambda i: tied[i]), dtype=np.uint32)
+        if ch == oracle.REVERSE or not np.array_equal(vo, exp_v):
+            return False
+        k, vo, ch, _ = oracle.sort(strict, v, profile=gb)
+        if ch != oracle.REVERSE or not np.array_equal(vo, v[::-1]) or not np.array_equal(k, np.sort(strict)):
+            return False
+        if oracle.sort(tied, profile=oracle.PAPER)[2] == oracle.REVERSE:
+            return False
         for row in read_golden("fsm_decisions.txt"):
             profile, n, span, h, desc, expect = row
             f = oracle.Features()
