@@ -145,6 +145,9 @@ typedef struct {
  * later tiles' bounded look-back waits run out (about a second) and the call
  * returns AHS_ERR_DEVICE_TIMEOUT with the context still usable. */
 #define AHS_DEBUG_STALL_ONE_TILE 1u
+/* Test hook: the feature pass counts its histogram a second time in the
+ * split layout, the path it takes when a packed 16-bit counter wraps. */
+#define AHS_DEBUG_K2_SPLIT 2u
 
 /* Filled by ahs_sort when non-NULL. */
 typedef struct {

@@ -26,6 +26,7 @@ AHS_U32, AHS_U64, AHS_I32, AHS_I64 = range(4)
 AHS_AUTO, AHS_IDENTITY, AHS_SMALL, AHS_COUNTING, AHS_RADIX, AHS_GENERAL, AHS_REVERSE = range(7)
 AHS_SEL_PAPER, AHS_SEL_LISTING6, AHS_SEL_GB300, AHS_SEL_MODEL, AHS_SEL_CUSTOM, AHS_SEL_LEMMA32 = range(6)
 AHS_DEBUG_STALL_ONE_TILE = 1
+AHS_DEBUG_K2_SPLIT = 2
 STRATEGY_NAMES = ("AUTO", "IDENTITY", "SMALL", "COUNTING", "RADIX", "GENERAL", "REVERSE")
 
 

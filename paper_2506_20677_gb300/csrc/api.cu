@@ -95,6 +95,11 @@ ahs_status run_features(ahs_ctx* ctx, const void* d_keys, uint64_t n, KeyDesc kd
     const size_t mark = ctx->tracer.records.size();
     cudaError_t e = launch_features(d_keys, n, kd, s, ctx->sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // A packed histogram counter wrapped: count again in the exact layout.
+    if (e == cudaSuccess && (ctx->h_rec->k2_wrapped || (ctx->cfg.debug_flags & AHS_DEBUG_K2_SPLIT))) {
+        e = launch_features_split_retry(d_keys, n, kd, s, ctx->sms, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) return cuda_status(ctx, e);
     // The histogram kernel returned at once for an input found presorted: its
     // trace entry processed no keys.

@@ -19,6 +19,10 @@ namespace {
 constexpr int kK1Threads = 512;
 template <typename K>
 struct K1Unroll { static constexpr int kU = 4; };
+// 64-bit keys: two vectors in flight per thread keep the counters and the
+// neighbours' keys in registers (three or four spill).
+template <>
+struct K1Unroll<uint64_t> { static constexpr int kU = 2; };
 constexpr int kK2Unroll = 4;
 // Up to this many bins K3 gives each bin a warp's lanes in eight warps that
 // split the slabs, instead of one thread per bin walking every slab: with few
@@ -171,6 +175,7 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
         rec->max_ord = gmx;
         rec->descents = gd;
         rec->ascents = ga;
+        rec->k2_wrapped = 0;
         rec->n = n;
         rec->span = span;
         rec->shift = s;
@@ -184,11 +189,12 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
 //  - nbins <= kU32Bins (43,692): every CTA counts all bins of the keys it
 //    reads, in R copies (warp w uses copy w % R) that spread the same-bin
 //    atomics of skewed inputs; one slab per CTA.
-//  - larger (up to 65,536 bins): the two CTAs of a cluster read the same
-//    chunks and each counts only its half of the bins (32,768 u32 counters,
-//    128 KB), so no counter needs more than 32 bits and no atomic is wider
-//    than 32 bits; the second read of a chunk is served by L2.  One slab per
-//    cluster.
+//  - larger (up to 65,536 bins), input in runs: the two CTAs of a cluster
+//    read the same chunks and each counts only its half of the bins (32,768
+//    u32 counters, 128 KB), so no counter needs more than 32 bits and no
+//    atomic is wider than 32 bits; the second read of a chunk is served by
+//    L2.  One slab per cluster.
+//  - larger, input not in runs: the packed layout (k2_packed below).
 template <typename K>
 __device__ __forceinline__ void k2_load(const K* __restrict__ body, uint64_t c, uint64_t nvec,
                                         Vec16<K> (&x)[kK2Unroll], bool (&ok)[kK2Unroll]) {
@@ -283,17 +289,103 @@ __device__ __forceinline__ void k2_split(const K* __restrict__ keys, uint64_t n,
     for (uint32_t j = threadIdx.x; j < len; j += kHistThreads) slab[j] = sm[j];
 }
 
+// Above kU32Bins bins, for an input not in runs (k2_packed_layout): every
+// CTA counts all bins of its own keys in 16-bit counters, two to a word
+// (128 KB).  A counter that reaches 2^15 gives 2^15 back at once and lists its
+// bin (the list adds 2^15 to the bin when the CTA writes its slab), so a
+// counter never holds more than 2^15 plus the additions that land before
+// that subtraction.  An addition that would carry out of 16 bits is seen by
+// the thread that makes it (old value 0xffff): the CTA marks the record and
+// the host counts again in the split layout, so the histogram is exact either
+// way.  One slab per CTA.  Inputs in runs (few descents or few ascents:
+// neighbouring keys share a bin) keep the split layout, whose additions need
+// no returned value: returning additions serialise when a warp's keys share a
+// counter.
+constexpr uint32_t kK2Words = kMaxBins / 2;
+constexpr uint32_t kK2OvfCap = 1024;   // flushes a CTA can list (2^15 keys each)
+static_assert((kK2Words + kK2OvfCap) * 4 <= kHistSmemBytes, "packed counters fit the shared memory");
+
+// K2's layout above kU32Bins: packed (one slab per CTA) or split (one slab
+// per cluster pair).  K3 asks the same question of the same record.
+__device__ __forceinline__ bool k2_packed_layout(const DevFeatures* rec, int split) {
+    const unsigned long long q = rec->n / 4;
+    return !split && rec->nbins > kU32Bins && rec->descents >= q && rec->ascents >= q;
+}
+
+template <typename K>
+__device__ __forceinline__ void k2_packed(const K* __restrict__ keys, uint64_t n, K flip,
+                                          uint64_t head, uint64_t nvec, K mn, uint32_t s,
+                                          uint32_t nb, uint32_t* __restrict__ slabs, uint32_t* sm,
+                                          uint32_t* wrapped) {
+    constexpr int V = Vec16<K>::kN;
+    constexpr uint64_t kChunkVecs = (uint64_t)kHistThreads * kK2Unroll;
+    __shared__ uint32_t s_novf, s_bad;
+    uint32_t* ovf = sm + kK2Words;
+    const uint32_t words = (nb + 1) >> 1;
+    for (uint32_t i = threadIdx.x; i < words; i += kHistThreads) sm[i] = 0;
+    if (threadIdx.x == 0) {
+        s_novf = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    auto add = [&](K x) {
+        const uint32_t bin = (uint32_t)(((K)(x ^ flip) - mn) >> s);
+        if (!AHS_DCHECK(bin < nb, "k2 bin", bin)) return;
+        const uint32_t sh = (bin & 1u) << 4;
+        const uint32_t old = (atomicAdd(&sm[bin >> 1], 1u << sh) >> sh) & 0xffffu;
+        if (old == 0x7fffu) {
+            atomicSub(&sm[bin >> 1], 0x8000u << sh);
+            const uint32_t i = atomicAdd(&s_novf, 1u);
+            if (i < kK2OvfCap) ovf[i] = bin;
+            else s_bad = 1;
+        } else if (old == 0xffffu) {
+            s_bad = 1;
+        }
+    };
+    if (blockIdx.x == 0) {
+        const uint64_t tail0 = head + nvec * V;
+        if (threadIdx.x < head) add(keys[threadIdx.x]);
+        if (threadIdx.x < n - tail0) add(keys[tail0 + threadIdx.x]);
+    }
+    const K* body = keys + head;
+    const uint64_t nchunks = ceil_div(nvec, kChunkVecs);
+    for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        Vec16<K> x[kK2Unroll];
+        bool ok[kK2Unroll];
+        k2_load(body, c, nvec, x, ok);
+#pragma unroll
+        for (int u = 0; u < kK2Unroll; ++u)
+            if (ok[u]) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) add(x[u].e[j]);
+            }
+    }
+    __syncthreads();
+    uint32_t* slab = slabs + (size_t)blockIdx.x * kMaxBins;
+    for (uint32_t j = threadIdx.x; j < words; j += kHistThreads) {
+        const uint32_t w = sm[j];
+        slab[2 * j] = w & 0xffffu;
+        if (2 * j + 1 < nb) slab[2 * j + 1] = w >> 16;
+    }
+    __syncthreads();   // the slab's plain stores come before the listed halves
+    const uint32_t novf = s_novf < kK2OvfCap ? s_novf : kK2OvfCap;
+    for (uint32_t i = threadIdx.x; i < novf; i += kHistThreads) atomicAdd(&slab[ovf[i]], 0x8000u);
+    if (threadIdx.x == 0 && s_bad) atomicExch(wrapped, 1u);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kHistThreads, 1)
 k2_histogram(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
-             const DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs, int skip_sorted) {
+             DevFeatures* __restrict__ rec, uint32_t* __restrict__ slabs, int skip_sorted, int split) {
     extern __shared__ __align__(16) uint32_t sm32[];
     if (presorted_skip(rec, (uint32_t)skip_sorted)) return;   // block-uniform
     const K mn = (K)rec->min_ord;
     const uint32_t s = rec->shift;
     const uint32_t nb = rec->nbins;
-    if (nb > kU32Bins) k2_split<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
-    else k2_replicated<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
+    if (nb <= kU32Bins) k2_replicated<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
+    else if (k2_packed_layout(rec, split))
+        k2_packed<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32, &rec->k2_wrapped);
+    else k2_split<K>(keys, n, flip, head, nvec, mn, s, nb, slabs, sm32);
 }
 
 // host_rec / host_hist (optional): pinned host mirrors of the record and of
@@ -302,7 +394,7 @@ __global__ void __launch_bounds__(256)
 k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
            DevFeatures* __restrict__ rec, unsigned long long* __restrict__ hist,
            double* __restrict__ partials, DevFeatures* host_rec,
-           unsigned long long* host_hist, int skip_sorted) {
+           unsigned long long* host_hist, int skip_sorted, int split) {
     if (presorted_skip(rec, (uint32_t)skip_sorted)) {
         // K2 counted nothing: no histogram, and the entropy is marked missing.
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -313,7 +405,8 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
         return;
     }
     const uint32_t nb = rec->nbins;
-    const uint32_t nslabs = nb > kU32Bins ? k2_grid / 2 : k2_grid;   // see K2's two layouts
+    // One slab per CTA (replicated and packed layouts) or per pair (split).
+    const uint32_t nslabs = (nb > kU32Bins && !k2_packed_layout(rec, split)) ? k2_grid / 2 : k2_grid;
     __shared__ double s_part[8];
     __shared__ bool s_last;
     __shared__ unsigned long long s_acc[8][32];
@@ -392,6 +485,10 @@ k3_entropy(const uint32_t* __restrict__ slabs, uint32_t k2_grid, uint64_t n,
 }
 
 template <typename K>
+cudaError_t k2_k3_t(const K* keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
+                    const FeatureScratch& s, int sms, cudaStream_t st, bool split);
+
+template <typename K>
 cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScratch& s, int sms,
                        cudaStream_t st) {
     const K* keys = static_cast<const K*>(keys_v);
@@ -404,8 +501,16 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
         k1_minmax_descents<K><<<g1, kK1Threads, 0, st>>>(keys, n, flip, head, nvec, s.k1_partials,
                                                           s.rec);
     }
-    // One CTA per SM (shared memory holds one histogram), launched as clusters
-    // of two so that a pair shares a GPC and its duplicated reads hit L2.
+    return k2_k3_t<K>(keys, n, flip, head, nvec, s, sms, st, false);
+}
+
+// K2 and K3.  One CTA per SM (shared memory holds one histogram), launched as
+// clusters of two so that a pair of the split layout shares a GPC and its
+// duplicated reads hit L2.  split: the split layout above kU32Bins whatever
+// the input (the exact count after a packed counter wrapped).
+template <typename K>
+cudaError_t k2_k3_t(const K* keys, uint64_t n, K flip, uint64_t head, uint64_t nvec,
+                    const FeatureScratch& s, int sms, cudaStream_t st, bool split) {
     const uint32_t g2 = (uint32_t)(sms & ~1);
     {
         TraceScope ts("features_histogram", n, st);
@@ -421,16 +526,27 @@ cudaError_t features_t(const void* keys_v, uint64_t n, K flip, const FeatureScra
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k2_histogram<K>, keys, n, flip, head, nvec,
-                                           (const DevFeatures*)s.rec, s.slabs, (int)s.skip_sorted);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k2_histogram<K>, keys, n, flip, head, nvec, s.rec,
+                                           s.slabs, (int)s.skip_sorted, (int)split);
         if (e != cudaSuccess) return e;
     }
     {
         TraceScope ts("features_entropy", 0, st);
         k3_entropy<<<kEntropyBlocks, 256, 0, st>>>(s.slabs, g2, n, s.rec, s.hist, s.ent_partials,
-                                                   s.host_rec, s.host_hist, (int)s.skip_sorted);
+                                                   s.host_rec, s.host_hist, (int)s.skip_sorted,
+                                                   (int)split);
     }
     return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t split_retry_t(const void* keys_v, uint64_t n, K flip, const FeatureScratch& s, int sms,
+                          cudaStream_t st) {
+    const K* keys = static_cast<const K*>(keys_v);
+    constexpr int V = Vec16<K>::kN;
+    const uint64_t head = head_elems<K>(keys, n);
+    const uint64_t nvec = (n - head) / V;
+    return k2_k3_t<K>(keys, n, flip, head, nvec, s, sms, st, true);
 }
 
 }  // namespace
@@ -465,6 +581,14 @@ cudaError_t launch_features(const void* keys, uint64_t n, KeyDesc kd, const Feat
                                          kHistSmemBytes);
     if (e != cudaSuccess) return e;
     return features_t<uint64_t>(keys, n, kd.flip, s, sms, st);
+}
+
+cudaError_t launch_features_split_retry(const void* keys, uint64_t n, KeyDesc kd,
+                                        const FeatureScratch& s, int sms, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&s.rec->k2_wrapped, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    if (kd.bytes == 4) return split_retry_t<uint32_t>(keys, n, (uint32_t)kd.flip, s, sms, st);
+    return split_retry_t<uint64_t>(keys, n, kd.flip, s, sms, st);
 }
 
 }  // namespace ahs

@@ -26,7 +26,7 @@ struct DevFeatures {
     uint32_t k1_done;             // last-block counters (return to 0 after each use)
     uint32_t k3_done;
     uint32_t rh_done;             // radix digit-histogram kernel
-    uint32_t pad0;
+    uint32_t k2_wrapped;          // a packed K2 counter wrapped: rerun K2 in the split layout
     unsigned long long pad[5];
 };
 static_assert(sizeof(DevFeatures) == 128, "DevFeatures layout");
@@ -69,6 +69,11 @@ uint32_t k1_blocks(uint64_t n, int sms);
 size_t features_scratch_bytes(int sms);
 cudaError_t launch_features(const void* keys, uint64_t n, KeyDesc kd, const FeatureScratch& s,
                             int sms, cudaStream_t st);
+// After launch_features, when the record says a packed histogram counter
+// wrapped (DevFeatures::k2_wrapped): K2 again in the exact split layout, then
+// K3.  The record's K1 results stay.
+cudaError_t launch_features_split_retry(const void* keys, uint64_t n, KeyDesc kd,
+                                        const FeatureScratch& s, int sms, cudaStream_t st);
 
 // ------------------------------------------------------------------ counting
 // Keys-only counting sort (Listing 2) from the exact histogram of the feature

@@ -107,6 +107,12 @@ extern "C" ahs_status ahs_features_noalloc(const void* d_keys, uint64_t n, ahs_k
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&r, fs.rec, sizeof(r), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // A packed histogram counter wrapped: count again in the exact layout.
+    if (e == cudaSuccess && r.k2_wrapped) {
+        e = ahs::launch_features_split_retry(d_keys, n, kd, fs, s->sms, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&r, fs.rec, sizeof(r), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? AHS_ERR_OOM : AHS_ERR_CUDA;
     h_out->n = r.n;
     h_out->min_bits = r.min_ord ^ kd.flip;
