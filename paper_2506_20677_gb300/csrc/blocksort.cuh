@@ -181,12 +181,12 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
 // can be sorted by one counting pass instead of LSD passes: count the keys by
 // the top DB bits of u = ord(x) - min (DB chosen so there is about one
 // counter per key), place each key at its counter's slot in shared memory,
-// then give each key its final place inside its sub-bucket by counting the
-// sub-bucket's keys that precede it (smaller, or equal and earlier).  This is
-// the counting sort of Section III-C over the leading bits with an
-// insertion-style rank for the rest.  A sub-bucket of more than
-// kCountRankMax keys with different offsets would make the rank quadratic;
-// such a bucket is sorted by block_sort's LSD passes instead.
+// then let each thread insertion-sort a range of about IPT staged keys made
+// of whole sub-buckets (already in order among themselves).  This is
+// the counting sort of Section III-C over the leading bits with an insertion
+// sort for the rest.  A sub-bucket of more than kCountRankMax keys with
+// different offsets would make the insertion sort quadratic; such a bucket is
+// sorted by block_sort's LSD passes instead.
 constexpr uint32_t kCountRankMax = 32;
 
 __host__ __device__ constexpr uint32_t pow2_at_least(uint32_t x) {
@@ -244,9 +244,11 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t wbase = warp * WARP_ITEMS;
 
-    // 2^lgm >= m counters at most; zero them before the first barrier.
-    const uint32_t lgm = m > 1 ? bitlen64(m - 1) : 0u;
-    for (uint32_t i = tid; i < cnt_pad(1u << lgm); i += THREADS) S.cnt[i] = 0;
+    // About one counter per key: at most 2^lgc counters, 0.8 m <= 2^lgc < 1.6 m
+    // (fewer counters to clear and scan; the insertion sort below meets
+    // slightly larger sub-buckets).  Zero them before the first barrier.
+    const uint32_t lgc = m > 1 ? bitlen64(m - 1 - m / 5) : 0u;
+    for (uint32_t i = tid; i < cnt_pad(1u << lgc); i += THREADS) S.cnt[i] = 0;
 
     K key[IPT];
     K lo = ~K(0), hi = 0;
@@ -263,7 +265,7 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
         }
     }
     {
-        const unsigned long long a = warp_min((unsigned long long)lo), b = warp_max((unsigned long long)hi);
+        const K a = warp_min(lo), b = warp_max(hi);
         if (lane == 0) { S.red[0][warp] = a; S.red[1][warp] = b; }
     }
     __syncthreads();
@@ -288,7 +290,7 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
         }
         return;
     }
-    const uint32_t DB = D < lgm ? D : lgm;   // lgm >= 1 here, since m >= 2
+    const uint32_t DB = D < lgc ? D : lgc;   // lgc >= 1 here, since m >= 2
     const uint32_t R = D - DB;
     const uint32_t nb = 1u << DB;
 
@@ -342,22 +344,58 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
         }
     }
     __syncthreads();
-    if (R == 0) {
-        // Each sub-bucket holds one value: the staged order is sorted.
-        for (uint32_t p = tid; p < m; p += THREADS) keys_out[p] = S.keys[p];
-        return;
-    }
-    for (uint32_t p = tid; p < m; p += THREADS) {
-        const K x = S.keys[p];
-        const K o = x ^ flip;
-        const uint32_t d = (uint32_t)((K)(o - lo) >> R);
-        const uint32_t b = S.cnt[cnt_pad(d)], e = S.cnt[cnt_pad(d + 1)];
-        uint32_t r = b;
-        for (uint32_t j = b; j < e; ++j) {
-            const K y = S.keys[j] ^ flip;
-            r += (y < o || (y == o && j < p)) ? 1u : 0u;
+    if (R > 0) {
+        // The staged keys are ordered by their leading DB bits; each
+        // sub-bucket is in arbitrary order.  Thread t insertion-sorts the
+        // staged keys from the first sub-bucket start at or after t (IPT + 1)
+        // to the first at or after (t + 1)(IPT + 1): whole sub-buckets, about
+        // IPT + 1 keys a thread, and an odd stride, so that the lanes of a
+        // warp read and write different banks.  (THREADS ranges cover m keys:
+        // m <= THREADS * IPT.)
+        constexpr uint32_t kStride = IPT + 1;
+        auto cut = [&](uint32_t q) -> uint32_t {
+            if (q >= m) return m;
+            const uint32_t d = (uint32_t)((K)((S.keys[q] ^ flip) - lo) >> R);
+            const uint32_t b = S.cnt[cnt_pad(d)];
+            return b == q ? q : S.cnt[cnt_pad(d + 1)];
+        };
+        const uint32_t s0 = cut(tid * kStride), s1 = cut(tid * kStride + kStride);
+        // In ordered values, the three largest keys so far stay in registers
+        // (w0 <= w1 <= w2): each key joins them and the smallest of the four
+        // goes to shared memory three places back, without a branch.  Only a
+        // key below the last one written (a sub-bucket of five keys or more)
+        // is inserted by shifting keys in memory.  The window starts with
+        // three copies of the smallest ordered value, whose places fall
+        // before s0 and are not written.
+        K w0 = 0, w1 = 0, w2 = 0, last = 0;
+        for (uint32_t i = s0; i < s1; ++i) {
+            const K o = S.keys[i] ^ flip;
+            if (o < last) {   // then i - 4 >= s0, and o < w0 <= w1 <= w2
+                uint32_t j = i - 3;
+                do {
+                    S.keys[j] = S.keys[j - 1];
+                    --j;
+                } while (j > s0 && (K)(S.keys[j - 1] ^ flip) > o);
+                S.keys[j] = o ^ flip;
+                continue;
+            }
+            const bool c0 = o < w0, c1 = o < w1, c2 = o < w2;
+            const K out = c0 ? o : w0;
+            w0 = c0 ? w0 : (c1 ? o : w1);
+            w1 = c1 ? w1 : (c2 ? o : w2);
+            w2 = c2 ? w2 : o;
+            if (i >= s0 + 3) S.keys[i - 3] = out ^ flip;
+            last = out;
         }
-        if (AHS_DCHECK(r < m, "count sort rank", r)) keys_out[r] = x;
+        if (s1 >= s0 + 3) S.keys[s1 - 3] = w0 ^ flip;
+        if (s1 >= s0 + 2) S.keys[s1 - 2] = w1 ^ flip;
+        if (s1 >= s0 + 1) S.keys[s1 - 1] = w2 ^ flip;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const uint32_t p = wbase + 32 * i + lane;
+        if (p < m) keys_out[p] = S.keys[p];
     }
 }
 

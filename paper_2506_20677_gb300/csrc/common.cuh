@@ -108,6 +108,15 @@ __device__ __forceinline__ T warp_max(T v) {
     }
     return v;
 }
+// 32-bit unsigned reductions in one warp-wide instruction.
+template <>
+__device__ __forceinline__ uint32_t warp_min<uint32_t>(uint32_t v) {
+    return __reduce_min_sync(AHS_FULL_MASK, v);
+}
+template <>
+__device__ __forceinline__ uint32_t warp_max<uint32_t>(uint32_t v) {
+    return __reduce_max_sync(AHS_FULL_MASK, v);
+}
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(AHS_FULL_MASK, v, o);
