@@ -189,6 +189,10 @@ __device__ __forceinline__ void block_sort(const K* keys_in, K* keys_out,
 // sorted by block_sort's LSD passes instead.
 constexpr uint32_t kCountRankMax = 32;
 
+__host__ __device__ constexpr uint32_t log2_floor(uint32_t x) {
+    return x > 1 ? 1 + log2_floor(x >> 1) : 0;
+}
+
 __host__ __device__ constexpr uint32_t pow2_at_least(uint32_t x) {
     uint32_t p = 1;
     while (p < x) p <<= 1;
@@ -199,12 +203,38 @@ __host__ __device__ constexpr uint32_t pow2_at_least(uint32_t x) {
 // consecutive counters then meets no bank conflict with its neighbours.
 __device__ __forceinline__ uint32_t cnt_pad(uint32_t i) { return i + (i >> 5); }
 
+// A run of C counters (C a power of two up to 32) starting at a multiple of C
+// lies inside one padded group of 32: its words are consecutive.
+template <uint32_t C>
+__device__ __forceinline__ uint32_t run_sum(const uint32_t* cnt, uint32_t c0, uint32_t& mx) {
+    const uint32_t* p = cnt + cnt_pad(c0);
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < C; ++k) {
+        const uint32_t v = p[k];
+        sum += v;
+        mx = v > mx ? v : mx;
+    }
+    return sum;
+}
+template <uint32_t C>
+__device__ __forceinline__ void run_starts(uint32_t* cnt, uint32_t c0, uint32_t run) {
+    uint32_t* p = cnt + cnt_pad(c0);
+#pragma unroll
+    for (uint32_t k = 0; k < C; ++k) {
+        const uint32_t v = p[k];
+        p[k] = run;
+        run += v;
+    }
+}
+
 template <typename K, int THREADS, int IPT>
 struct BlockCountSmem {
     static constexpr int W = THREADS / 32;
     static constexpr uint32_t CAP = THREADS * IPT;
     static constexpr uint32_t NB = pow2_at_least(CAP);
-    uint32_t cnt[NB + NB / 32 + 1];   // counts, then run starts; [cnt_pad(nb)] = m
+    static_assert(NB % 128 == 0, "counters are cleared as 16-byte words");
+    alignas(16) uint32_t cnt[NB + NB / 32 + 4];   // counts, then run starts; [cnt_pad(nb)] = m
     uint32_t scan[W + 1];
     unsigned long long red[2][W];
     K keys[CAP];
@@ -248,7 +278,11 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
     // (fewer counters to clear and scan; the insertion sort below meets
     // slightly larger sub-buckets).  Zero them before the first barrier.
     const uint32_t lgc = m > 1 ? bitlen64(m - 1 - m / 5) : 0u;
-    for (uint32_t i = tid; i < cnt_pad(1u << lgc); i += THREADS) S.cnt[i] = 0;
+    {
+        uint4* z = reinterpret_cast<uint4*>(S.cnt);
+        for (uint32_t i = tid; i < (cnt_pad(1u << lgc) + 3) / 4; i += THREADS)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
 
     K key[IPT];
     K lo = ~K(0), hi = 0;
@@ -311,21 +345,43 @@ __device__ __forceinline__ void block_sort_keys(const K* keys_in, K* keys_out, u
     __syncthreads();
 
     // Exclusive scan of the nb counters: thread t owns a run of C of them.
+    // With a power-of-two block and nb >= THREADS, C = nb / THREADS is a
+    // power of two (at most 32) and the runs are unrolled.
     const uint32_t C = (nb + THREADS - 1) / THREADS;
     const uint32_t c0 = tid * C < nb ? tid * C : nb;
     const uint32_t c1 = c0 + C < nb ? c0 + C : nb;
+    constexpr uint32_t kLgT = log2_floor(THREADS);
+    const int lgC = ((THREADS & (THREADS - 1)) == 0 && nb >= THREADS) ? (int)(DB - kLgT) : -1;
     uint32_t sum = 0, mx = 0;
-    for (uint32_t c = c0; c < c1; ++c) {
-        const uint32_t v = S.cnt[cnt_pad(c)];
-        sum += v;
-        mx = v > mx ? v : mx;
+    switch (lgC) {
+        case 0: sum = run_sum<1>(S.cnt, c0, mx); break;
+        case 1: sum = run_sum<2>(S.cnt, c0, mx); break;
+        case 2: sum = run_sum<4>(S.cnt, c0, mx); break;
+        case 3: sum = run_sum<8>(S.cnt, c0, mx); break;
+        case 4: sum = run_sum<16>(S.cnt, c0, mx); break;
+        case 5: sum = run_sum<32>(S.cnt, c0, mx); break;
+        default:
+            for (uint32_t c = c0; c < c1; ++c) {
+                const uint32_t v = S.cnt[cnt_pad(c)];
+                sum += v;
+                mx = v > mx ? v : mx;
+            }
     }
     uint32_t total;
     uint32_t run = block_exclusive_scan<THREADS>(sum, S.scan, &total);
-    for (uint32_t c = c0; c < c1; ++c) {
-        const uint32_t v = S.cnt[cnt_pad(c)];
-        S.cnt[cnt_pad(c)] = run;
-        run += v;
+    switch (lgC) {
+        case 0: run_starts<1>(S.cnt, c0, run); break;
+        case 1: run_starts<2>(S.cnt, c0, run); break;
+        case 2: run_starts<4>(S.cnt, c0, run); break;
+        case 3: run_starts<8>(S.cnt, c0, run); break;
+        case 4: run_starts<16>(S.cnt, c0, run); break;
+        case 5: run_starts<32>(S.cnt, c0, run); break;
+        default:
+            for (uint32_t c = c0; c < c1; ++c) {
+                const uint32_t v = S.cnt[cnt_pad(c)];
+                S.cnt[cnt_pad(c)] = run;
+                run += v;
+            }
     }
     if (tid == 0) S.cnt[cnt_pad(nb)] = m;
     if (__syncthreads_or(R > 0 && mx > kCountRankMax)) {
