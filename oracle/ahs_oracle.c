@@ -197,13 +197,13 @@ uint32_t orc_radix_passes(uint64_t span) {
     return d;
 }
 
-/* ---------------------------------------------------- Listing 1: insertion sort */
+/* ----------------------------------------------- Section III-E: insertion sort */
 
 static void insertion_core(val_t* a, uint32_t* v, uint64_t n) {
     for (uint64_t i = 1; i < n; ++i) {
         val_t key = a[i];
         uint32_t kv = v ? v[i] : 0;
-        uint64_t j = i;                      /* j - 1 plays the listing's j */
+        uint64_t j = i;                      /* a[0, i) is sorted; find key's place */
         while (j > 0 && a[j - 1] > key) {    /* strict > keeps equal keys in order */
             a[j] = a[j - 1];
             if (v) v[j] = v[j - 1];
@@ -264,7 +264,7 @@ int orc_counting_sort(const void* keys, void* out, const uint32_t* vals, uint32_
     return ORC_OK;
 }
 
-/* ------------------------------------------------------- Listing 3: LSD radix sort */
+/* -------------------------------------------------- Section III-G: LSD radix sort */
 
 /* LSD over u = x - min in base 256 (the base the paper uses for k > 10^6),
  * d = ceil(log_256 k) passes (Eq. 4).  Each pass distributes the keys into 256
@@ -310,9 +310,10 @@ int orc_radix_sort(const void* keys, void* out, const uint32_t* vals, uint32_t* 
     return rc;
 }
 
-/* Listing 7 (keys only): split negatives and non-negatives, sort the absolute
- * values of the negatives and the non-negatives separately, reverse the
- * former, restore their sign and concatenate.  Negation is exact in 128 bits. */
+/* Section III-K, Listing 7 (keys only): split negatives and non-negatives,
+ * sort the absolute values of the negatives and the non-negatives separately,
+ * reverse the former, restore their sign and concatenate.  Negation is exact
+ * in 128 bits. */
 int orc_radix_sort_signed_listing7(const void* keys, void* out, uint64_t n, int t) {
     if (!valid_type(t)) return ORC_EINVAL;
     val_t* a = load_all(keys, n, t);
@@ -336,7 +337,7 @@ int orc_radix_sort_signed_listing7(const void* keys, void* out, uint64_t n, int 
     return rc;
 }
 
-/* ------------------------------------ Listing 4: quicksort, median-of-three pivot */
+/* ----------------------------- Section III-G(1): quicksort, median-of-three pivot */
 
 static val_t median_of_three(const val_t* a, uint64_t n) {
     val_t x = a[0], y = a[n / 2], z = a[n - 1];
@@ -347,8 +348,8 @@ static val_t median_of_three(const val_t* a, uint64_t n) {
     return y;
 }
 
-/* Partition into (< pivot), (== pivot), (> pivot), each in input order, as the
- * listing's filters do; the (== pivot) group keeps every copy of the pivot. */
+/* Partition into (< pivot), (== pivot), (> pivot), each in input order; the
+ * (== pivot) group keeps every copy of the pivot. */
 static void quick_core(val_t* a, val_t* tmp, uint64_t n) {
     while (n > 1) {
         val_t pivot = median_of_three(a, n);
