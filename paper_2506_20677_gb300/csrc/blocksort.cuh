@@ -3,7 +3,8 @@
 // min, with min and the digit count taken from the keys themselves (so a
 // segment whose keys are all equal costs no pass).  Used for small inputs
 // (the paper's insertion-sort regime, Section III-E) and for the buckets of the
-// general path.
+// general path.  Without a payload a counting pass on the leading bits and
+// per-thread insertion sorts take its place (block_sort_keys, below).
 #pragma once
 
 #include "common.cuh"
