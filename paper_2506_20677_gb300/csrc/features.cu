@@ -67,31 +67,42 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
     if (gtid < head) k1_scalar(keys, gtid, n, flip, mn, mx, desc, asc);
     if (gtid < n - tail0) k1_scalar(keys, tail0 + gtid, n, flip, mn, mx, desc, asc);
 
-    // Vector body; lanes of a warp hold consecutive vectors, so the pair that
-    // straddles two vectors is closed with a shuffle.  Lane 31 (and the owner
-    // of the last vector) needs the next vector's first key from memory: it is
-    // loaded together with the vectors so its latency overlaps theirs.
+    // Vector body: each warp reads kK1Unroll * 32 consecutive vectors per
+    // iteration (one contiguous stretch), vector u * 32 + lane to each lane, so
+    // the pair that straddles two vectors is closed with a shuffle from the
+    // next lane, or for lane 31 from lane 0's next vector.  The last lane of
+    // the stretch (and the owner of the last vector) needs the next key from
+    // memory: it is loaded together with the vectors so its latency overlaps
+    // theirs.
     const K* body = keys + head;
     uint32_t dloc = 0, aloc = 0;   // descents, ascents of this thread (< 2^32 keys per thread)
     constexpr int kK1Unroll = K1Unroll<K>::kU;
-    for (uint64_t wb = gtid - lane; wb < nvec; wb += stride * kK1Unroll) {
+    constexpr uint64_t kRun = 32ull * kK1Unroll;   // vectors of a warp's stretch
+    const uint64_t nwarps = stride >> 5;
+    for (uint64_t cb = (gtid >> 5) * kRun; cb < nvec; cb += nwarps * kRun) {
         Vec16<K> x[kK1Unroll];
-        K succ[kK1Unroll];
-        bool ok[kK1Unroll];
+        K first[kK1Unroll];
+        K succ = K(0);
 #pragma unroll
         for (int u = 0; u < kK1Unroll; ++u) {
-            const uint64_t v = wb + lane + (uint64_t)u * stride;
-            ok[u] = v < nvec;
-            if (ok[u]) x[u] = load_vec16_stream(body + v * V);
+            const uint64_t v = cb + (uint64_t)u * 32 + lane;
+            if (v < nvec) x[u] = load_vec16_stream(body + v * V);
             const uint64_t e_next = head + (v + 1) * V;
-            succ[u] = (ok[u] && (lane == 31 || v + 1 == nvec) && e_next < n) ? keys[e_next] : K(0);
+            if (v < nvec && (v + 1 == nvec || (lane == 31 && u == kK1Unroll - 1)) && e_next < n)
+                succ = keys[e_next];
         }
 #pragma unroll
         for (int u = 0; u < kK1Unroll; ++u) {
-            const uint64_t v = wb + lane + (uint64_t)u * stride;
-            const K first = ok[u] ? (K)(x[u].e[0] ^ flip) : K(0);
-            const K nxt = __shfl_down_sync(AHS_FULL_MASK, first, 1);
-            if (ok[u]) {
+            const uint64_t v = cb + (uint64_t)u * 32 + lane;
+            first[u] = v < nvec ? (K)(x[u].e[0] ^ flip) : K(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kK1Unroll; ++u) {
+            const uint64_t v = cb + (uint64_t)u * 32 + lane;
+            const K down = __shfl_down_sync(AHS_FULL_MASK, first[u], 1);
+            const K wrap = u + 1 < kK1Unroll ? __shfl_sync(AHS_FULL_MASK, first[u + 1 < kK1Unroll ? u + 1 : u], 0)
+                                             : K(0);
+            if (v < nvec) {
                 K o[V];
 #pragma unroll
                 for (int j = 0; j < V; ++j) {
@@ -105,7 +116,10 @@ k1_minmax_descents(const K* __restrict__ keys, uint64_t n, K flip, uint64_t head
                     aloc += (o[j] < o[j + 1]) ? 1u : 0u;
                 }
                 if (head + (v + 1) * V < n) {
-                    const K on = (lane < 31 && v + 1 < nvec) ? nxt : (K)(succ[u] ^ flip);
+                    K on;
+                    if (v + 1 == nvec) on = (K)(succ ^ flip);
+                    else if (lane < 31) on = down;
+                    else on = u + 1 < kK1Unroll ? wrap : (K)(succ ^ flip);
                     dloc += (o[V - 1] > on) ? 1u : 0u;
                     aloc += (o[V - 1] < on) ? 1u : 0u;
                 }
